@@ -1,0 +1,93 @@
+/*
+ * amqft: batched power-of-two complex DFT by the AM-QFT recursion
+ * ("A class of AM-QFT algorithms for power-of-two FFT", Pasquini),
+ * computed by hand-written CUDA kernels for sm_103a (GB300).
+ *
+ * The transform is the DFT of Eq. qft_0A,
+ *     X(k) = sum_{n=0}^{N-1} x(n) exp(-2*pi*i*n*k/N),   N = 2^log2n,
+ * computed by one of the 8 AM-QFT variants (Sect. 5-6): the D_c / D_r
+ * decompositions (Sect. 3.1-3.2), the D_k / D_n separations and H_k / H_n
+ * halvings (Tab. 3-4), and the odd-to-even conversion M_variant (Tab. 5-6).
+ *
+ * Conventions for every entry point:
+ *   - Data are interleaved complex (re, im), transform-major: transform b
+ *     occupies elements [b*N, (b+1)*N).  AMQFT_C64 elements are 2 x float32
+ *     (8 bytes); in and out must be 8-byte aligned device pointers.
+ *   - in and out are owned by the caller; they must not overlap.
+ *   - stream is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     asynchronous on that stream and make no host synchronisation.
+ *   - Return value: AMQFT_OK (0) or a negative AMQFT_ERR_* code; the
+ *     message of the last error on the calling thread is amqft_last_error().
+ *   - The inverse is unnormalised: inv(fwd(x)) = N * x.  Since every AM-QFT
+ *     constant is real, it is computed as conj(F(conj(x))), which is also the
+ *     adjoint F^H used for gradients.
+ */
+#ifndef AMQFT_H
+#define AMQFT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define AMQFT_OK 0
+#define AMQFT_ERR_N (-1)        /* log2n outside the supported range */
+#define AMQFT_ERR_VARIANT (-2)  /* variant not in 1..8 */
+#define AMQFT_ERR_DTYPE (-3)    /* dtype not supported by this entry point */
+#define AMQFT_ERR_ALIGN (-4)    /* pointer misaligned or NULL */
+#define AMQFT_ERR_INPLACE (-5)  /* in and out overlap */
+#define AMQFT_ERR_CUDA (-6)     /* a CUDA call or kernel launch failed */
+#define AMQFT_ERR_DEVICE (-7)   /* device is not sm_103 or lacks resources */
+#define AMQFT_ERR_ARG (-8)      /* other invalid argument (NULL plan, batch < 0, ...) */
+#define AMQFT_ERR_NOMEM (-9)    /* host or device allocation failed */
+
+#define AMQFT_LOG2N_MAX 16      /* largest log2n of the fused single-pass kernels */
+
+typedef enum { AMQFT_C64 = 0, AMQFT_CBF16 = 1, AMQFT_CF16 = 2 } amqft_dtype;
+
+typedef struct amqft_plan_s *amqft_plan_t;
+
+/* Create a plan for `batch` transforms of length 2^log2n with AM-QFT
+ * variant `variant` (1..8, Sect. 6) and storage `dtype`.
+ * The plan owns the variant's trig-constant table (Sect. 7.1: the
+ * M/8 constants 2cos, 1/(2cos), 2sin or 1/(2sin) of theta*(2j+1) for every
+ * periodisation M = 16..N, N/4 - 2 floats in all) on the current device.
+ * Errors: AMQFT_ERR_N (log2n < 0 or > AMQFT_LOG2N_MAX), AMQFT_ERR_VARIANT,
+ * AMQFT_ERR_DTYPE, AMQFT_ERR_ARG (out NULL or batch < 0), AMQFT_ERR_DEVICE,
+ * AMQFT_ERR_NOMEM, AMQFT_ERR_CUDA.  On error *out is set to NULL. */
+int amqft_plan(amqft_plan_t *out, int log2n, int variant, int64_t batch, int dtype);
+
+/* Forward transform of the plan's batch: out = DFT(in), Eq. qft_0A.
+ * exp_out is reserved for 16-bit storage (per-transform exponents) and must
+ * be NULL for AMQFT_C64.  Errors: AMQFT_ERR_ARG, AMQFT_ERR_ALIGN,
+ * AMQFT_ERR_INPLACE, AMQFT_ERR_DTYPE, AMQFT_ERR_CUDA (launch failure). */
+int amqft_exec_fwd(amqft_plan_t plan, const void *in, void *out, int32_t *exp_out, void *stream);
+
+/* Unnormalised inverse / adjoint: out = conj(DFT(conj(in))) = N * IDFT(in).
+ * exp_in / exp_out are reserved for 16-bit storage and must be NULL for
+ * AMQFT_C64.  Errors as amqft_exec_fwd. */
+int amqft_exec_inv(amqft_plan_t plan, const void *in, const int32_t *exp_in, void *out,
+                   int32_t *exp_out, void *stream);
+
+/* Release the plan and its device constant table.  NULL is accepted. */
+int amqft_destroy(amqft_plan_t plan);
+
+/* Message of the last error on the calling thread ("" if none).  The string
+ * stays valid until the next amqft call on the same thread. */
+const char *amqft_last_error(void);
+
+/* Library build/version string. */
+const char *amqft_version(void);
+
+/* Kernel configuration the plan selected, for tests and benchmarks:
+ * cluster size (CTAs per transform, 1 when a CTA holds whole transforms),
+ * transforms per CTA, threads per CTA, dynamic shared memory bytes per CTA.
+ * Any out pointer may be NULL. */
+int amqft_plan_info(amqft_plan_t plan, int *cluster, int *per_cta, int *threads, int *smem_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AMQFT_H */

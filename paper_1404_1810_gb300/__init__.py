@@ -1,0 +1,7 @@
+"""GB300-native AM-QFT: batched power-of-two complex DFT by the AM-QFT
+recursion ("A class of AM-QFT algorithms for power-of-two FFT", Pasquini),
+computed by hand-written sm_103a CUDA kernels behind a C ABI (include/amqft.h).
+"""
+from .amqft import (AMQFT_C64, AMQFT_CBF16, AMQFT_CF16, AmqftError, Plan, amqft_destroy,  # noqa: F401
+                    amqft_exec_fwd, amqft_exec_inv, amqft_last_error, amqft_plan, amqft_plan_info,
+                    amqft_version, fft, load)

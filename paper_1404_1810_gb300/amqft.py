@@ -1,0 +1,173 @@
+"""Thin Python binding of libamqft.so: the C-ABI entry points under the same
+names, plus a small torch convenience layer (argument marshalling only --
+every step of the transform runs in the library's CUDA kernels).
+
+There is no fallback: if the compiled library is missing the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+AMQFT_C64, AMQFT_CBF16, AMQFT_CF16 = 0, 1, 2
+ERRORS = {
+    -1: "AMQFT_ERR_N", -2: "AMQFT_ERR_VARIANT", -3: "AMQFT_ERR_DTYPE", -4: "AMQFT_ERR_ALIGN",
+    -5: "AMQFT_ERR_INPLACE", -6: "AMQFT_ERR_CUDA", -7: "AMQFT_ERR_DEVICE", -8: "AMQFT_ERR_ARG",
+    -9: "AMQFT_ERR_NOMEM",
+}
+LIB_PATH = _build.LIB
+
+_lock = threading.Lock()
+_lib = None
+
+
+class AmqftError(RuntimeError):
+    def __init__(self, code: int, where: str, msg: str):
+        super().__init__(f"{where}: {ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+def load(path: str | None = None) -> ctypes.CDLL:
+    """Load libamqft.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libamqft.so not found at {p}: run paper_1404_1810_gb300.build.build() first")
+        lib = ctypes.CDLL(p)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64
+        lib.amqft_plan.argtypes = [ctypes.POINTER(vp), i32, i32, i64, i32]
+        lib.amqft_plan.restype = i32
+        lib.amqft_exec_fwd.argtypes = [vp, vp, vp, vp, vp]
+        lib.amqft_exec_fwd.restype = i32
+        lib.amqft_exec_inv.argtypes = [vp, vp, vp, vp, vp, vp]
+        lib.amqft_exec_inv.restype = i32
+        lib.amqft_destroy.argtypes = [vp]
+        lib.amqft_destroy.restype = i32
+        lib.amqft_last_error.restype = ctypes.c_char_p
+        lib.amqft_version.restype = ctypes.c_char_p
+        lib.amqft_plan_info.argtypes = [vp] + [ctypes.POINTER(i32)] * 4
+        lib.amqft_plan_info.restype = i32
+        _lib = lib
+        return lib
+
+
+def _check(rc: int, where: str) -> None:
+    if rc != 0:
+        raise AmqftError(rc, where, load().amqft_last_error().decode())
+
+
+# --- the C-ABI entry points, same names, plain integers for pointers ------
+
+def amqft_plan(log2n: int, variant: int, batch: int, dtype: int = AMQFT_C64) -> int:
+    h = ctypes.c_void_p()
+    _check(load().amqft_plan(ctypes.byref(h), int(log2n), int(variant), int(batch), int(dtype)), "amqft_plan")
+    return int(h.value)
+
+
+def amqft_exec_fwd(plan: int, d_in: int, d_out: int, exp_out: int = 0, stream: int = 0) -> None:
+    _check(load().amqft_exec_fwd(plan, d_in, d_out, exp_out or None, stream or None), "amqft_exec_fwd")
+
+
+def amqft_exec_inv(plan: int, d_in: int, exp_in: int, d_out: int, exp_out: int = 0, stream: int = 0) -> None:
+    _check(load().amqft_exec_inv(plan, d_in, exp_in or None, d_out, exp_out or None, stream or None),
+           "amqft_exec_inv")
+
+
+def amqft_destroy(plan: int) -> None:
+    _check(load().amqft_destroy(plan), "amqft_destroy")
+
+
+def amqft_last_error() -> str:
+    return load().amqft_last_error().decode()
+
+
+def amqft_version() -> str:
+    return load().amqft_version().decode()
+
+
+def amqft_plan_info(plan: int) -> dict:
+    vals = [ctypes.c_int() for _ in range(4)]
+    _check(load().amqft_plan_info(plan, *[ctypes.byref(v) for v in vals]), "amqft_plan_info")
+    return dict(zip(("cluster", "per_cta", "threads", "smem_bytes"), (v.value for v in vals)))
+
+
+# --- torch convenience layer ------------------------------------------------
+
+def _stream_handle(stream) -> int:
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return int(stream.cuda_stream)
+
+
+class Plan:
+    """Owns one amqft plan; fwd/inv take complex64 CUDA tensors (batch, N)."""
+
+    def __init__(self, log2n: int, variant: int, batch: int, dtype: int = AMQFT_C64):
+        self.log2n, self.variant, self.batch, self.dtype = int(log2n), int(variant), int(batch), int(dtype)
+        self.n = 1 << self.log2n
+        self.handle = amqft_plan(self.log2n, self.variant, self.batch, self.dtype)
+
+    def info(self) -> dict:
+        return amqft_plan_info(self.handle)
+
+    def _check_tensor(self, t, name):
+        import torch
+
+        if t.dtype != torch.complex64 or not t.is_cuda or not t.is_contiguous():
+            raise ValueError(f"{name} must be a contiguous complex64 CUDA tensor")
+        if t.numel() != self.batch * self.n:
+            raise ValueError(f"{name} has {t.numel()} elements, plan needs {self.batch * self.n}")
+
+    def fwd(self, x, out=None, stream=None):
+        import torch
+
+        self._check_tensor(x, "x")
+        if out is None:
+            out = torch.empty_like(x)
+        self._check_tensor(out, "out")
+        amqft_exec_fwd(self.handle, x.data_ptr(), out.data_ptr(), 0, _stream_handle(stream))
+        return out
+
+    def inv(self, x, out=None, stream=None):
+        import torch
+
+        self._check_tensor(x, "x")
+        if out is None:
+            out = torch.empty_like(x)
+        self._check_tensor(out, "out")
+        amqft_exec_inv(self.handle, x.data_ptr(), 0, out.data_ptr(), 0, _stream_handle(stream))
+        return out
+
+    def close(self):
+        if getattr(self, "handle", 0):
+            amqft_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fft(x, variant: int = 4, inverse: bool = False):
+    """DFT (or unnormalised inverse) over the last axis of a complex64 CUDA tensor."""
+    n = x.shape[-1]
+    log2n = n.bit_length() - 1
+    if n != 1 << log2n:
+        raise ValueError("length must be a power of two")
+    xc = x.reshape(-1, n).contiguous()
+    p = Plan(log2n, variant, xc.shape[0])
+    try:
+        y = p.inv(xc) if inverse else p.fwd(xc)
+    finally:
+        p.close()
+    return y.reshape(x.shape)

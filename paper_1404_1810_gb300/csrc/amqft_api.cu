@@ -1,0 +1,251 @@
+// C ABI of the AM-QFT library (include/amqft.h): plans, constant tables,
+// argument checks and kernel dispatch.  No compute happens on the host
+// except the trig-constant table of a plan.
+#include <math.h>
+#include <stdarg.h>
+#include <new>
+#include <stdint.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <string>
+
+#include "../../include/amqft.h"
+#include "amqft_device.cuh"
+#include "amqft_internal.h"
+
+namespace amqft {
+
+FusedConfig fused_config(int logN) {
+  FusedConfig c;
+  const int N = 1 << logN, half = N >> 1;
+  const int padded = half + 2;
+  // regions of 64 or more values are padded to whole 32-float rows so the
+  // shared-memory swizzle stays inside the region
+  c.RS = logN >= 7 ? ((padded + 31) / 32) * 32 : ((padded + 1) / 2) * 2;
+  if (logN <= 13) {
+    c.cluster = 1;
+    c.threads = 512;
+    // a pass touches regions * N/4 values; 512 threads x 16 values each
+    const int tpc = (512 * 16) / (N >= 4 ? N : 4);
+    c.per_cta = tpc < 1 ? 1 : tpc;
+    c.nreg = 4 * c.per_cta;
+  } else {
+    c.cluster = 4;
+    c.per_cta = 1;
+    c.nreg = 1;
+    c.threads = logN == 14 ? 256 : (logN == 15 ? 512 : 1024);
+  }
+  c.tot_off = ((c.nreg * c.RS + 31) / 32) * 32;
+  c.smem = (c.tot_off + c.threads + 32) * (int)sizeof(float);
+  return c;
+}
+
+static cudaError_t fused_launch(int variant, const FusedArgs& a, const SmallConsts& K, const FusedConfig& c,
+                                cudaStream_t st) {
+  switch (variant) {
+    case 1: return launch_variant_1(a, K, c, st);
+    case 2: return launch_variant_2(a, K, c, st);
+    case 3: return launch_variant_3(a, K, c, st);
+    case 4: return launch_variant_4(a, K, c, st);
+    case 5: return launch_variant_5(a, K, c, st);
+    case 6: return launch_variant_6(a, K, c, st);
+    case 7: return launch_variant_7(a, K, c, st);
+    default: return launch_variant_8(a, K, c, st);
+  }
+}
+
+// N = 1: the DFT is the identity (conjugated twice for the inverse).
+__global__ void copy1_kernel(const float2* __restrict__ in, float2* __restrict__ out, long long batch) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < batch) out[i] = in[i];
+}
+
+}  // namespace amqft
+
+using namespace amqft;
+
+// ---------------------------------------------------------------------
+// trig constants (Sect. 7.1), computed on the host in long double from the
+// exact turn fraction and rounded once to float
+// ---------------------------------------------------------------------
+static const long double kTwoPi = 6.283185307179586476925286766559005768394L;
+
+// cos(2*pi*num/den), den a power of two >= 8: the angle is folded into
+// [0, pi/4] with exact integer arithmetic before the libm call.
+static long double cos_frac(long long num, long long den) {
+  long long r = num % den;
+  if (r < 0) r += den;
+  if (2 * r > den) r = den - r;                  // [0, 1/2] turn
+  long double sign = 1.0L;
+  if (4 * r > den) { r = den / 2 - r; sign = -1.0L; }   // [0, 1/4] turn
+  if (8 * r > den) return sign * sinl(kTwoPi * (long double)(den / 4 - r) / (long double)den);
+  return sign * cosl(kTwoPi * (long double)r / (long double)den);
+}
+
+static long double sin_frac(long long num, long long den) { return cos_frac(den / 4 - num, den); }
+
+// Constant of variant v at angle 2*pi*(2j+1)/M: 2cos (1,3), 1/(2cos) (2,4),
+// 2sin (5,7), 1/(2sin) (6,8).
+static float variant_const(int v, long long M, long long j) {
+  const long long p = 2 * j + 1;
+  long double c;
+  switch (v) {
+    case 1: case 3: c = 2.0L * cos_frac(p, M); break;
+    case 2: case 4: c = 1.0L / (2.0L * cos_frac(p, M)); break;
+    case 5: case 7: c = 2.0L * sin_frac(p, M); break;
+    default: c = 1.0L / (2.0L * sin_frac(p, M)); break;
+  }
+  return (float)c;
+}
+
+// ---------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------
+static thread_local std::string t_err;
+
+static int fail(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return code;
+}
+
+static int cuda_fail(cudaError_t e, const char* what) {
+  return fail(AMQFT_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct amqft_plan_s {
+  int log2n;
+  int variant;
+  int64_t batch;
+  int dtype;
+  int device;
+  float* d_ctab;
+  SmallConsts small;
+  FusedConfig cfg;
+};
+
+extern "C" {
+
+const char* amqft_last_error(void) { return t_err.c_str(); }
+
+const char* amqft_version(void) { return "amqft 0.1 (sm_103a, fused single-pass, float32)"; }
+
+int amqft_plan(amqft_plan_t* out, int log2n, int variant, int64_t batch, int dtype) {
+  t_err.clear();
+  if (!out) return fail(AMQFT_ERR_ARG, "amqft_plan: out is NULL");
+  *out = nullptr;
+  if (log2n < 0 || log2n > AMQFT_LOG2N_MAX)
+    return fail(AMQFT_ERR_N, "amqft_plan: log2n=%d outside [0, %d]", log2n, AMQFT_LOG2N_MAX);
+  if (variant < 1 || variant > 8) return fail(AMQFT_ERR_VARIANT, "amqft_plan: variant=%d not in 1..8", variant);
+  if (dtype != AMQFT_C64) return fail(AMQFT_ERR_DTYPE, "amqft_plan: dtype=%d not supported (AMQFT_C64 only)", dtype);
+  if (batch < 0) return fail(AMQFT_ERR_ARG, "amqft_plan: batch=%lld < 0", (long long)batch);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "amqft_plan: cudaGetDevice");
+  cudaDeviceProp prop;
+  e = cudaGetDeviceProperties(&prop, dev);
+  if (e != cudaSuccess) return cuda_fail(e, "amqft_plan: cudaGetDeviceProperties");
+  if (!(prop.major == 10 && prop.minor == 3))
+    return fail(AMQFT_ERR_DEVICE, "amqft_plan: device %d is sm_%d%d, this library is built for sm_103a", dev,
+                prop.major, prop.minor);
+  amqft_plan_s* p = new (std::nothrow) amqft_plan_s();
+  if (!p) return fail(AMQFT_ERR_NOMEM, "amqft_plan: host allocation failed");
+  p->log2n = log2n;
+  p->variant = variant;
+  p->batch = batch;
+  p->dtype = dtype;
+  p->device = dev;
+  p->d_ctab = nullptr;
+  // level-major table: periodisation M = 16..N holds M/8 constants at [M/8-2, M/4-2)
+  const long long N = 1LL << log2n;
+  const long long ntab = N >= 16 ? N / 4 - 2 : 0;
+  const long long nhost = ntab > (long long)(LEAF - 2) ? ntab : (long long)(LEAF - 2);
+  float* h = (float*)calloc((size_t)nhost, sizeof(float));
+  if (!h) { delete p; return fail(AMQFT_ERR_NOMEM, "amqft_plan: host allocation failed"); }
+  for (long long M = 16; M / 8 - 2 < nhost; M *= 2)
+    for (long long j = 0; j < M / 8 && M / 8 - 2 + j < nhost; ++j) h[M / 8 - 2 + j] = variant_const(variant, M, j);
+  for (int i = 0; i < LEAF - 2; ++i) p->small.c[i] = h[i];
+  p->small.cos_pi4 = (float)cos_frac(1, 8);
+  if (ntab > 0) {
+    e = cudaMalloc(&p->d_ctab, (size_t)ntab * sizeof(float));
+    if (e != cudaSuccess) { free(h); delete p; return cuda_fail(e, "amqft_plan: cudaMalloc(constant table)"); }
+    e = cudaMemcpy(p->d_ctab, h, (size_t)ntab * sizeof(float), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) { free(h); cudaFree(p->d_ctab); delete p; return cuda_fail(e, "amqft_plan: cudaMemcpy"); }
+  }
+  free(h);
+  if (log2n >= 1) p->cfg = fused_config(log2n);
+  else memset(&p->cfg, 0, sizeof p->cfg);
+  *out = p;
+  return AMQFT_OK;
+}
+
+static int exec(amqft_plan_t p, const void* in, void* out, int inverse, const void* e1, const void* e2,
+                void* stream) {
+  t_err.clear();
+  if (!p) return fail(AMQFT_ERR_ARG, "plan is NULL");
+  if (e1 || e2) return fail(AMQFT_ERR_DTYPE, "exponent arrays are only used with 16-bit storage");
+  if (p->batch == 0) return AMQFT_OK;
+  if (!in || !out) return fail(AMQFT_ERR_ALIGN, "in or out is NULL");
+  if (((uintptr_t)in | (uintptr_t)out) & 7u) return fail(AMQFT_ERR_ALIGN, "in/out must be 8-byte aligned");
+  const long long N = 1LL << p->log2n;
+  const uintptr_t bytes = (uintptr_t)(N * p->batch * 8);
+  const uintptr_t a0 = (uintptr_t)in, b0 = (uintptr_t)out;
+  if (a0 < b0 + bytes && b0 < a0 + bytes) return fail(AMQFT_ERR_INPLACE, "in and out overlap");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  if (p->log2n == 0) {
+    const unsigned grid = (unsigned)((p->batch + 255) / 256);
+    copy1_kernel<<<grid, 256, 0, st>>>((const float2*)in, (float2*)out, p->batch);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e, "copy1_kernel launch");
+    return AMQFT_OK;
+  }
+  FusedArgs a;
+  a.in = (const float2*)in;
+  a.out = (float2*)out;
+  a.ctab = p->d_ctab;
+  a.batch = p->batch;
+  a.logN = p->log2n;
+  a.tpc = p->cfg.per_cta;
+  a.inverse = inverse;
+  a.RS = p->cfg.RS;
+  a.tot_off = p->cfg.tot_off;
+  e = fused_launch(p->variant, a, p->small, p->cfg, st);
+  if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
+  return AMQFT_OK;
+}
+
+int amqft_exec_fwd(amqft_plan_t p, const void* in, void* out, int32_t* exp_out, void* stream) {
+  return exec(p, in, out, 0, exp_out, nullptr, stream);
+}
+
+int amqft_exec_inv(amqft_plan_t p, const void* in, const int32_t* exp_in, void* out, int32_t* exp_out,
+                   void* stream) {
+  return exec(p, in, out, 1, exp_in, exp_out, stream);
+}
+
+int amqft_destroy(amqft_plan_t p) {
+  t_err.clear();
+  if (!p) return AMQFT_OK;
+  if (p->d_ctab) cudaFree(p->d_ctab);
+  delete p;
+  return AMQFT_OK;
+}
+
+int amqft_plan_info(amqft_plan_t p, int* cluster, int* per_cta, int* threads, int* smem_bytes) {
+  t_err.clear();
+  if (!p) return fail(AMQFT_ERR_ARG, "plan is NULL");
+  if (cluster) *cluster = p->cfg.cluster;
+  if (per_cta) *per_cta = p->cfg.per_cta;
+  if (threads) *threads = p->cfg.threads;
+  if (smem_bytes) *smem_bytes = p->cfg.smem;
+  return AMQFT_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,9 @@
+// Fused AM-QFT kernels of variant 4 (instantiated in a translation unit of
+// their own so the eight variants compile in parallel).
+#include "amqft_fused_impl.cuh"
+
+namespace amqft {
+cudaError_t launch_variant_4(const FusedArgs& a, const SmallConsts& K, const FusedConfig& c, cudaStream_t st) {
+  return launch_v<4>(a, K, c, st);
+}
+}  // namespace amqft

@@ -1,0 +1,45 @@
+"""Helpers shared by the GPU tests: run the CUDA library through its C ABI and
+derive the float32 tolerances from the oracle's own float32 evaluation."""
+from __future__ import annotations
+
+import numpy as np
+
+COS_FAMILY = (1, 2, 3, 4)
+SCAN_VARIANTS = (1, 3, 5, 7)      # recurrences: chunked scans on wide levels
+EXACT_VARIANTS = (2, 4, 6, 8)     # no recurrence: same float32 ops as the recursion
+
+
+def rel(a, b) -> float:
+    a = np.asarray(a, dtype=np.complex128)
+    b = np.asarray(b, dtype=np.complex128)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def north_star_tol(log2n: int) -> float:
+    """rel-L2 bound stated for float32: 2e-7 * log2 N."""
+    return 2e-7 * max(1, log2n)
+
+
+def derived_tol(e32: float, log2n: int) -> float:
+    """float32 tolerance against the float64 oracle: the stated bound where the
+    algorithm itself meets it, otherwise twice the error of the paper's own
+    recursion evaluated in float32 (same inputs, sequential order)."""
+    return max(north_star_tol(log2n), 2.0 * e32)
+
+
+def run_gpu(x: np.ndarray, variant: int, inverse: bool = False) -> np.ndarray:
+    """x: (B, N) complex -> (B, N) complex128 result of the CUDA library."""
+    import torch
+
+    from paper_1404_1810_gb300 import Plan
+
+    xb = np.ascontiguousarray(np.atleast_2d(x).astype(np.complex64))
+    b, n = xb.shape
+    xt = torch.from_numpy(xb).cuda()
+    plan = Plan(n.bit_length() - 1, variant, b)
+    try:
+        y = plan.inv(xt) if inverse else plan.fwd(xt)
+        torch.cuda.synchronize()
+    finally:
+        plan.close()
+    return y.cpu().numpy().astype(np.complex128)

@@ -1,0 +1,188 @@
+"""Parity of the CUDA AM-QFT path against the CPU oracle (GB300 only).
+
+Bars:
+  * variants 2, 4, 6, 8 (no recurrences) must be bit-identical to the
+    oracle's float32 instantiation of the recursion, on every sample;
+  * every variant must be within the float32 tolerance of the float64
+    oracle: 2e-7*log2N where the recursion itself reaches it in float32,
+    otherwise twice the float32 error of the recursion (derived, per input);
+  * variants 5 and 7 (sine constants + recurrences) lose all accuracy in
+    float32 beyond N ~ 2^9 (Sect. 7.3), so their tolerance check stops there.
+"""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import (EXACT_VARIANTS, SCAN_VARIANTS, derived_tol, north_star_tol, rel, run_gpu)
+
+pytestmark = pytest.mark.gpu
+VARIANTS = list(range(1, 9))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    import torch
+
+    from paper_1404_1810_gb300 import build, load
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    return load()
+
+
+def batch_for(log2n):
+    # several CTAs, plus a ragged last CTA for the small sizes
+    if log2n <= 6:
+        return 2 * (8192 >> max(log2n, 2)) + 3
+    if log2n <= 12:
+        return 37
+    return 5
+
+
+def check_one(orc, x, v, log2n, inverse=False):
+    sign = +1 if inverse else -1
+    y = run_gpu(x, v, inverse=inverse)
+    for b in range(x.shape[0]):
+        r32 = orc.amqft(x[b].astype(np.complex64).astype(np.complex128), v, prec="f32", sign=sign)
+        r64 = orc.amqft(x[b].astype(np.complex64).astype(np.complex128), v, prec="f64", sign=sign)
+        if v in EXACT_VARIANTS:
+            assert np.array_equal(y[b].astype(np.complex64), r32.astype(np.complex64)), \
+                f"v{v} N=2^{log2n} transform {b}: not bit-identical to the float32 recursion"
+        e32 = rel(r32, r64)
+        if v in (5, 7) and log2n > 9:
+            assert np.all(np.isfinite(y[b])) or not np.all(np.isfinite(r32))
+            continue
+        tol = derived_tol(e32, log2n)
+        assert rel(y[b], r64) <= tol, f"v{v} N=2^{log2n} b={b}: {rel(y[b], r64):.3e} > {tol:.3e}"
+
+
+@pytest.mark.parametrize("v", VARIANTS)
+@pytest.mark.parametrize("log2n", range(1, 17))
+def test_forward_matches_oracle(orc, v, log2n):
+    n = 1 << log2n
+    b = batch_for(log2n)
+    x = synth.normal_complex(n, b, config=2, stream=log2n)
+    # the oracle is run on a sample of the batch: first, middle and last rows
+    rows = sorted({0, b // 2, b - 1})
+    y_all = run_gpu(x, v)
+    xs = x[rows]
+    for i, row in enumerate(rows):
+        r32 = orc.amqft(xs[i].astype(np.complex64).astype(np.complex128), v, prec="f32")
+        r64 = orc.amqft(xs[i].astype(np.complex64).astype(np.complex128), v, prec="f64")
+        if v in EXACT_VARIANTS:
+            assert np.array_equal(y_all[row].astype(np.complex64), r32.astype(np.complex64)), (v, log2n, row)
+        if v in (5, 7) and log2n > 9:
+            continue
+        tol = derived_tol(rel(r32, r64), log2n)
+        assert rel(y_all[row], r64) <= tol, (v, log2n, row, rel(y_all[row], r64), tol)
+
+
+@pytest.mark.parametrize("v", VARIANTS)
+@pytest.mark.parametrize("log2n", [1, 2, 3, 5, 8, 10, 13, 14, 16])
+def test_inverse_matches_oracle(orc, v, log2n):
+    x = synth.uniform_complex(1 << log2n, 2, config=1, stream=200 + log2n)
+    check_one(orc, x, v, log2n, inverse=True)
+
+
+@pytest.mark.parametrize("v", [1, 2, 3, 4])
+@pytest.mark.parametrize("log2n", [4, 10, 16])
+def test_roundtrip(v, log2n):
+    n = 1 << log2n
+    x = synth.uniform_complex(n, 3, config=1, stream=300 + log2n)
+    y = run_gpu(x, v)
+    z = run_gpu(y, v, inverse=True)
+    # twice the forward error of the float32 recursion (about 1e-5 at 2^16)
+    tol = 3.0 * max(north_star_tol(log2n), 1.2e-5 if log2n >= 14 else 0.0)
+    assert rel(z, n * x) < tol
+
+
+@pytest.mark.parametrize("v", [2, 4])
+def test_closed_forms_on_gpu(v):
+    n = 4096
+    k = np.arange(n)
+    x = np.zeros((3, n), complex)
+    x[0, 0] = 1.0                   # impulse at 0 -> all ones
+    x[1, 5] = 1.0                   # impulse at 5 -> exp(-2 pi i 5 k / N)
+    x[2] = np.exp(2j * np.pi * np.mod(7 * k, n) / n)   # tone -> N delta(k-7)
+    y = run_gpu(x, v)
+    assert np.max(np.abs(y[0] - 1.0)) < 1e-6
+    assert np.max(np.abs(y[1] - np.exp(-2j * np.pi * np.mod(5 * k, n) / n))) < 1e-5
+    assert np.max(np.abs(y[2] - n * (k == 7))) < 1e-5 * n
+
+
+def test_config1_n1024_all_variants(orc):
+    """Single complex DFT N = 1024, Re/Im iid U[-1,1), all 8 variants, against
+    the long double naive DFT and the float64 recursion."""
+    x = synth.uniform_complex(1024, 1, config=1)
+    truth = orc.naive_dft(x[0].astype(np.complex64).astype(np.complex128))
+    for v in VARIANTS:
+        y = run_gpu(x, v)[0]
+        r32 = orc.amqft(x[0].astype(np.complex64).astype(np.complex128), v, prec="f32")
+        if v in EXACT_VARIANTS:
+            assert np.array_equal(y.astype(np.complex64), r32.astype(np.complex64))
+        if v in (5, 7):
+            continue
+        assert rel(y, truth) <= derived_tol(rel(r32, truth), 10)
+
+
+def test_bench_size_sampled(orc):
+    """The bench workload (N = 2^16, batch 4096, N(0,1)) in the bench's launch
+    configuration, checked on sampled transforms."""
+    import torch
+
+    from paper_1404_1810_gb300 import Plan
+
+    n, b = 1 << 16, 4096
+    x = synth.device_normal_complex64(n, b, "cuda")
+    for v in (4, 2, 1):
+        p = Plan(16, v, b)
+        y = p.fwd(x)
+        torch.cuda.synchronize()
+        for row in (0, 1, 2047, 4095):
+            xr = x[row].cpu().numpy().astype(np.complex128)
+            r32 = orc.amqft(xr, v, prec="f32")
+            r64 = orc.amqft(xr, v, prec="f64")
+            yr = y[row].cpu().numpy().astype(np.complex128)
+            if v in EXACT_VARIANTS:
+                assert np.array_equal(yr.astype(np.complex64), r32.astype(np.complex64)), (v, row)
+            assert rel(yr, r64) <= derived_tol(rel(r32, r64), 16), (v, row)
+        p.close()
+
+
+def test_empty_batch_and_errors():
+    import torch
+
+    from paper_1404_1810_gb300 import AmqftError, Plan, amqft_exec_fwd, amqft_plan
+
+    p = Plan(10, 4, 0)
+    x = torch.zeros(0, dtype=torch.complex64, device="cuda")
+    amqft_exec_fwd(p.handle, x.data_ptr(), x.data_ptr(), 0, 0)   # batch 0: no-op
+    p.close()
+    with pytest.raises(AmqftError) as e:
+        amqft_plan(10, 9, 1)
+    assert e.value.code == -2
+    with pytest.raises(AmqftError) as e:
+        amqft_plan(17, 4, 1)
+    assert e.value.code == -1
+    with pytest.raises(AmqftError) as e:
+        amqft_plan(10, 4, 1, 7)
+    assert e.value.code == -3
+    p = Plan(10, 4, 2)
+    buf = torch.zeros(4 * 1024 + 8, dtype=torch.complex64, device="cuda")
+    with pytest.raises(AmqftError) as e:          # misaligned by 4 bytes
+        amqft_exec_fwd(p.handle, buf.data_ptr() + 4, buf.data_ptr() + 2 * 8 * 1024 + 16, 0, 0)
+    assert e.value.code == -4
+    with pytest.raises(AmqftError) as e:          # overlapping in/out
+        amqft_exec_fwd(p.handle, buf.data_ptr(), buf.data_ptr() + 8 * 1024, 0, 0)
+    assert e.value.code == -5
+    p.close()
+
+
+@pytest.mark.parametrize("log2n", [0, 1, 2])
+def test_tiny_lengths(orc, log2n):
+    x = synth.uniform_complex(1 << log2n, 5, stream=9)
+    for v in VARIANTS:
+        y = run_gpu(x, v)
+        for b in range(5):
+            r32 = orc.amqft(x[b].astype(np.complex64).astype(np.complex128), v, prec="f32")
+            assert np.array_equal(y[b].astype(np.complex64), r32.astype(np.complex64))

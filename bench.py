@@ -169,8 +169,8 @@ def cpu_baseline(x_host_rows, variant, sign_pair=True):
     s = min(s, x_host_rows.shape[0])
     rows = np.ascontiguousarray(x_host_rows[:s])
     t0 = time.perf_counter()
-    y, threads = oracle.amqft_batch(rows, variant, threads=0)
-    oracle.amqft_batch(y, variant, threads=0, sign=+1)
+    y, threads = oracle.amqft_batch(rows, variant, threads=cores)
+    oracle.amqft_batch(y, variant, threads=cores, sign=+1)
     dt = time.perf_counter() - t0
     return {"value": 2 * s * n / dt / 1e9, "unit": UNIT, "cores": int(threads), "kind": "oracle",
             "sample": f"{s} transforms of N={n} forward + inverse, float64 AM-QFT variant {variant}, "
@@ -194,12 +194,12 @@ def run_reference(args):
     s = cores  # one forward + one inverse transform per core per step
     x = synth.normal_complex(n, s, config=2, stream=0)
     for _ in range(args.warmup):
-        y, thr = oracle.amqft_batch(x, args.variant, threads=0)
-        oracle.amqft_batch(y, args.variant, threads=0, sign=+1)
+        y, thr = oracle.amqft_batch(x, args.variant, threads=cores)
+        oracle.amqft_batch(y, args.variant, threads=cores, sign=+1)
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        y, thr = oracle.amqft_batch(x, args.variant, threads=0)
-        oracle.amqft_batch(y, args.variant, threads=0, sign=+1)
+        y, thr = oracle.amqft_batch(x, args.variant, threads=cores)
+        oracle.amqft_batch(y, args.variant, threads=cores, sign=+1)
     dt = time.perf_counter() - t0
     value = 2 * s * n * args.steps / dt / 1e9
     line = {

@@ -42,7 +42,8 @@ extern "C" {
 #define AMQFT_ERR_ARG (-8)      /* other invalid argument (NULL plan, batch < 0, ...) */
 #define AMQFT_ERR_NOMEM (-9)    /* host or device allocation failed */
 
-#define AMQFT_LOG2N_MAX 16      /* largest log2n of the fused single-pass kernels */
+#define AMQFT_LOG2N_FUSED_MAX 16 /* largest log2n of the fused single-pass kernels */
+#define AMQFT_LOG2N_MAX 24       /* largest log2n (multi-pass above 2^16, variants 2, 4, 6, 8) */
 
 typedef enum { AMQFT_C64 = 0, AMQFT_CBF16 = 1, AMQFT_CF16 = 2 } amqft_dtype;
 
@@ -53,7 +54,13 @@ typedef struct amqft_plan_s *amqft_plan_t;
  * The plan owns the variant's trig-constant table (Sect. 7.1: the
  * M/8 constants 2cos, 1/(2cos), 2sin or 1/(2sin) of theta*(2j+1) for every
  * periodisation M = 16..N, N/4 - 2 floats in all) on the current device.
- * Errors: AMQFT_ERR_N (log2n < 0 or > AMQFT_LOG2N_MAX), AMQFT_ERR_VARIANT,
+ * Lengths up to 2^AMQFT_LOG2N_FUSED_MAX run in one fused kernel (one HBM
+ * read and write per sample).  Longer transforms (variants 2, 4, 6, 8 only:
+ * the others contain recurrences) run as several passes over a workspace the
+ * plan allocates: two buffers of the transform's size per transform of a
+ * chunk, at most 2 GiB, the batch processed chunk by chunk.
+ * Errors: AMQFT_ERR_N (log2n < 0 or > AMQFT_LOG2N_MAX), AMQFT_ERR_VARIANT
+ * (also variants 1, 3, 5, 7 with log2n > AMQFT_LOG2N_FUSED_MAX),
  * AMQFT_ERR_DTYPE, AMQFT_ERR_ARG (out NULL or batch < 0), AMQFT_ERR_DEVICE,
  * AMQFT_ERR_NOMEM, AMQFT_ERR_CUDA.  On error *out is set to NULL. */
 int amqft_plan(amqft_plan_t *out, int log2n, int variant, int64_t batch, int dtype);

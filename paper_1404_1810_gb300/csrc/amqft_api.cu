@@ -11,8 +11,8 @@
 
 #include <string>
 
-#include "../../include/amqft.h"
-#include "amqft_device.cuh"
+#include "amqft.h"
+#include "amqft_multipass_impl.cuh"
 #include "amqft_internal.h"
 
 namespace amqft {
@@ -27,18 +27,18 @@ FusedConfig fused_config(int logN) {
   if (logN <= 13) {
     c.cluster = 1;
     c.threads = 512;
-    // a pass touches regions * N/4 values; 512 threads x 16 values each
-    const int tpc = (512 * 16) / (N >= 4 ? N : 4);
+    // a CTA holds 16384 region values: 512 threads x 32 values
+    const int tpc = (512 * 32) / (N >= 4 ? 2 * N : 8);
     c.per_cta = tpc < 1 ? 1 : tpc;
     c.nreg = 4 * c.per_cta;
   } else {
     c.cluster = 4;
     c.per_cta = 1;
     c.nreg = 1;
-    c.threads = logN == 14 ? 256 : (logN == 15 ? 512 : 1024);
+    c.threads = half / 32;  // 32 region values per thread
   }
   c.tot_off = ((c.nreg * c.RS + 31) / 32) * 32;
-  c.smem = (c.tot_off + c.threads + 32) * (int)sizeof(float);
+  c.smem = (c.tot_off + c.threads + 32 + snap_floats(c.nreg * half)) * (int)sizeof(float);
   return c;
 }
 
@@ -53,6 +53,16 @@ static cudaError_t fused_launch(int variant, const FusedArgs& a, const SmallCons
     case 6: return launch_variant_6(a, K, c, st);
     case 7: return launch_variant_7(a, K, c, st);
     default: return launch_variant_8(a, K, c, st);
+  }
+}
+
+static cudaError_t multipass_launch(int variant, const MpArgs& a, float* W0, float* W1, const SmallConsts& K,
+                                    cudaStream_t st) {
+  switch (variant) {
+    case 2: return multipass_variant_2(a, W0, W1, K, st);
+    case 4: return multipass_variant_4(a, W0, W1, K, st);
+    case 6: return multipass_variant_6(a, W0, W1, K, st);
+    default: return multipass_variant_8(a, W0, W1, K, st);
   }
 }
 
@@ -128,7 +138,14 @@ struct amqft_plan_s {
   float* d_ctab;
   SmallConsts small;
   FusedConfig cfg;
+  // multi-pass path: two ping-pong workspaces of chunk * 4 regions
+  float* d_work;
+  long long chunk;
+  long long RSg;
 };
+
+// workspace budget of one plan (both ping-pong buffers)
+static const long long kWorkspaceBytes = 2LL << 30;
 
 extern "C" {
 
@@ -143,6 +160,10 @@ int amqft_plan(amqft_plan_t* out, int log2n, int variant, int64_t batch, int dty
   if (log2n < 0 || log2n > AMQFT_LOG2N_MAX)
     return fail(AMQFT_ERR_N, "amqft_plan: log2n=%d outside [0, %d]", log2n, AMQFT_LOG2N_MAX);
   if (variant < 1 || variant > 8) return fail(AMQFT_ERR_VARIANT, "amqft_plan: variant=%d not in 1..8", variant);
+  if (log2n > AMQFT_LOG2N_FUSED_MAX && (variant & 1))
+    return fail(AMQFT_ERR_VARIANT,
+                "amqft_plan: variant %d (a recurrence variant) is limited to log2n <= %d; "
+                "variants 2, 4, 6, 8 reach %d", variant, AMQFT_LOG2N_FUSED_MAX, AMQFT_LOG2N_MAX);
   if (dtype != AMQFT_C64) return fail(AMQFT_ERR_DTYPE, "amqft_plan: dtype=%d not supported (AMQFT_C64 only)", dtype);
   if (batch < 0) return fail(AMQFT_ERR_ARG, "amqft_plan: batch=%lld < 0", (long long)batch);
   int dev = 0;
@@ -162,6 +183,9 @@ int amqft_plan(amqft_plan_t* out, int log2n, int variant, int64_t batch, int dty
   p->dtype = dtype;
   p->device = dev;
   p->d_ctab = nullptr;
+  p->d_work = nullptr;
+  p->chunk = 0;
+  p->RSg = 0;
   // level-major table: periodisation M = 16..N holds M/8 constants at [M/8-2, M/4-2)
   const long long N = 1LL << log2n;
   const long long ntab = N >= 16 ? N / 4 - 2 : 0;
@@ -179,8 +203,23 @@ int amqft_plan(amqft_plan_t* out, int log2n, int variant, int64_t batch, int dty
     if (e != cudaSuccess) { free(h); cudaFree(p->d_ctab); delete p; return cuda_fail(e, "amqft_plan: cudaMemcpy"); }
   }
   free(h);
-  if (log2n >= 1) p->cfg = fused_config(log2n);
+  if (log2n >= 1 && log2n <= AMQFT_LOG2N_FUSED_MAX) p->cfg = fused_config(log2n);
   else memset(&p->cfg, 0, sizeof p->cfg);
+  if (log2n > AMQFT_LOG2N_FUSED_MAX && batch > 0) {
+    const long long half = N / 2;
+    p->RSg = ((half + 2 + 31) / 32) * 32;
+    const long long per_t = 2LL * 4 * p->RSg * (long long)sizeof(float);
+    long long chunk = kWorkspaceBytes / per_t;
+    if (chunk < 1) chunk = 1;
+    if (chunk > batch) chunk = batch;
+    p->chunk = chunk;
+    e = cudaMalloc(&p->d_work, (size_t)(chunk * per_t));
+    if (e != cudaSuccess) {
+      if (p->d_ctab) cudaFree(p->d_ctab);
+      delete p;
+      return cuda_fail(e, "amqft_plan: cudaMalloc(workspace)");
+    }
+  }
   *out = p;
   return AMQFT_OK;
 }
@@ -199,6 +238,23 @@ static int exec(amqft_plan_t p, const void* in, void* out, int inverse, const vo
   if (a0 < b0 + bytes && b0 < a0 + bytes) return fail(AMQFT_ERR_INPLACE, "in and out overlap");
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;
+  if (p->log2n > AMQFT_LOG2N_FUSED_MAX) {
+    const long long per_buf = p->chunk * 4 * p->RSg;
+    for (long long t0 = 0; t0 < p->batch; t0 += p->chunk) {
+      MpArgs a;
+      a.in = (const float2*)in;
+      a.out = (float2*)out;
+      a.ctab = p->d_ctab;
+      a.nt = (p->batch - t0) < p->chunk ? (p->batch - t0) : p->chunk;
+      a.t0 = t0;
+      a.logN = p->log2n;
+      a.inverse = inverse;
+      a.RSg = p->RSg;
+      e = multipass_launch(p->variant, a, p->d_work, p->d_work + per_buf, p->small, st);
+      if (e != cudaSuccess) return cuda_fail(e, "multi-pass launch");
+    }
+    return AMQFT_OK;
+  }
   if (p->log2n == 0) {
     const unsigned grid = (unsigned)((p->batch + 255) / 256);
     copy1_kernel<<<grid, 256, 0, st>>>((const float2*)in, (float2*)out, p->batch);
@@ -234,6 +290,7 @@ int amqft_destroy(amqft_plan_t p) {
   t_err.clear();
   if (!p) return AMQFT_OK;
   if (p->d_ctab) cudaFree(p->d_ctab);
+  if (p->d_work) cudaFree(p->d_work);
   delete p;
   return AMQFT_OK;
 }

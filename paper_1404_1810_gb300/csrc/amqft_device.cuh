@@ -78,7 +78,7 @@ struct Var {
 // ---------------------------------------------------------------------
 // small helpers
 // ---------------------------------------------------------------------
-__device__ __forceinline__ int sw(int p) { return p ^ (((p >> 5) ^ (p >> 10)) & 31); }
+__device__ __forceinline__ int sw(int p) { return p ^ ((p >> 5) & 31); }
 
 __device__ __forceinline__ int brev(int x, int bits) {
   return bits ? (int)(__brev((unsigned)x) >> (32 - bits)) : 0;
@@ -498,7 +498,7 @@ __device__ __noinline__ void run_tail(float* R, int ctx0, int logN, const SmallC
 template <int V>
 __device__ __noinline__ void run_leaf(float* R, int p0, int ctx, const SmallConsts& K) {
   float x[LEAF];
-  const int f = ((p0 >> 5) ^ (p0 >> 10)) & 31;  // sw() of a LEAF-aligned row
+  const int f = (p0 >> 5) & 31;  // sw() of a LEAF-aligned row
   if constexpr (Var<V>::ot) {
 #pragma unroll
     for (int e = 0; e < LEAF; ++e) x[e] = R[p0 + (e ^ f)];
@@ -517,65 +517,99 @@ __device__ __noinline__ void run_leaf(float* R, int p0, int ctx, const SmallCons
 // ---------------------------------------------------------------------
 // block-wide passes over all regions of the CTA (one tree level each)
 // ---------------------------------------------------------------------
+// Shared-memory geometry.  Region mode (sub == 0): nreg chain-layout
+// regions of N/2 (+2) values.  Node mode (sub > 0): one tree node of sub
+// values at [0, sub) whose root context is gbase & 1 (a subproblem of the
+// multi-pass path).
 struct Geo {
-  int logN, half, RS, nreg, gbase;
+  int logN, half, RS, nreg, gbase, sub;
 };
 
-__device__ __forceinline__ int ctx_of(const Geo& g, int r) { return (g.gbase + r) & 1; }
+// context of region (or node) r: region mode, C1 S1 C2 S2 alternate DCT/DST;
+// node mode, gbase is a bit mask of the nodes' root contexts
+__device__ __forceinline__ int ctx_of(const Geo& g, int r) {
+  return g.sub ? ((g.gbase >> r) & 1) : ((g.gbase + r) & 1);
+}
 
-// D_k time phase + M_v time phase (ot variants) at node size 2^logLp; in-place
-// quartets {i, L-1-i, H-1-i, H+i} so no barrier is needed inside the pass.
-template <int V, int TPB>
-__device__ __forceinline__ void pass_fwd_ot(float* sm, const Geo& g, int logLp, const float* __restrict__ ctab) {
-  const int Lp = 1 << logLp, H = Lp >> 1, logQ = logLp - 2, Q = 1 << logQ;
-  const unsigned nb = (unsigned)(g.half >> logLp) - 1u;
-  const unsigned Wr = nb << logQ, W = Wr * (unsigned)g.nreg;
-  const Div dv(Wr);
-  const float* __restrict__ ct = ctab + (H - 2);
-  for (unsigned w = threadIdx.x; w < W; w += TPB) {
-    const unsigned r = dv(w), rem = w - r * Wr;
-    const int b = (int)(rem >> logQ), i = (int)(rem & (Q - 1)), i2 = H - 1 - i;
-    float* R = sm + r * g.RS;
-    const int p0 = b << logLp;
-    const int ctx = node_ctx<V>(p0, logLp, g.half, ctx_of(g, r));
-    const int pa = sw(p0 + i), pb = sw(p0 + Lp - 1 - i), pc = sw(p0 + i2), pd = sw(p0 + H + i);
-    const float u0 = R[pa], w0 = R[pb], u1 = R[pc], w1 = R[pd];
-    const float c0 = __ldg(ct + i), c1 = __ldg(ct + i2);
-    if (ctx == 0) {
-      R[pa] = u0 + w0; R[pd] = (u0 - w0) * c0;
-      R[pc] = u1 + w1; R[pb] = (u1 - w1) * c1;
-    } else {
-      R[pd] = u0 - w0; R[pa] = (u0 + w0) * c0;
-      R[pb] = u1 - w1; R[pc] = (u1 + w1) * c1;
-    }
+// class-0 nodes of size 2^logLp: blocks [0, half - Lp) in region mode, the
+// whole node range [0, sub) in node mode
+__device__ __forceinline__ unsigned nodes_at(const Geo& g, int logLp) {
+  return g.sub ? (unsigned)(g.sub >> logLp) : (unsigned)(g.half >> logLp) - 1u;
+}
+
+template <int V>
+__device__ __forceinline__ int node_ctx_g(const Geo& g, int p0, int logLp, int ctx0) {
+  if constexpr (!Var<V>::flip) {
+    return ctx0;
+  } else {
+    if (g.sub) return (1 << logLp) == g.sub ? ctx0 : ((p0 >> logLp) & 1);
+    return node_ctx<V>(p0, logLp, g.half, ctx0);
   }
 }
 
-// D_n frequency phase + M_v frequency phase (to variants), in-place quartets.
+// D_k time phase + M_v time phase (ot variants) at node size 2^logLp, one
+// in-place quartet {i, L-1-i, H-1-i, H+i} of the node at p0.
+template <int V>
+__device__ __forceinline__ void fwd_ot_quartet(float* R, int p0, int logLp, int ctx, int i,
+                                               const float* __restrict__ ctab) {
+  const int Lp = 1 << logLp, H = Lp >> 1, i2 = H - 1 - i;
+  const float* __restrict__ ct = ctab + (H - 2);
+  const int pa = sw(p0 + i), pb = sw(p0 + Lp - 1 - i), pc = sw(p0 + i2), pd = sw(p0 + H + i);
+  const float u0 = R[pa], w0 = R[pb], u1 = R[pc], w1 = R[pd];
+  const float c0 = __ldg(ct + i), c1 = __ldg(ct + i2);
+  if (ctx == 0) {
+    R[pa] = u0 + w0; R[pd] = (u0 - w0) * c0;
+    R[pc] = u1 + w1; R[pb] = (u1 - w1) * c1;
+  } else {
+    R[pd] = u0 - w0; R[pa] = (u0 + w0) * c0;
+    R[pb] = u1 - w1; R[pc] = (u1 + w1) * c1;
+  }
+}
+
+// D_n frequency phase + M_v frequency phase (to variants), one in-place quartet.
+template <int V>
+__device__ __forceinline__ void bwd_to_quartet(float* R, int p0, int logLp, int ctx, int j,
+                                               const float* __restrict__ ctab) {
+  const int Lp = 1 << logLp, H = Lp >> 1, j2 = H - 1 - j;
+  const float* __restrict__ ct = ctab + (H - 2);
+  const int pa = sw(p0 + j), pb = sw(p0 + H + j), pc = sw(p0 + j2), pd = sw(p0 + Lp - 1 - j);
+  const float c0 = __ldg(ct + j), c1 = __ldg(ct + j2);
+  if (ctx == 0) {
+    const float e0 = R[pa], o0 = R[pb] * c0, e1 = R[pc], o1 = R[pd] * c1;
+    R[pa] = e0 + o0; R[pd] = e0 - o0;
+    R[pc] = e1 + o1; R[pb] = e1 - o1;
+  } else {
+    const float o0 = R[pa] * c0, e0 = R[pb], o1 = R[pc] * c1, e1 = R[pd];
+    R[pa] = o0 + e0; R[pd] = o0 - e0;
+    R[pc] = o1 + e1; R[pb] = o1 - e1;
+  }
+}
+
 template <int V, int TPB>
-__device__ __forceinline__ void pass_bwd_to(float* sm, const Geo& g, int logLp, const float* __restrict__ ctab) {
-  const int Lp = 1 << logLp, H = Lp >> 1, logQ = logLp - 2, Q = 1 << logQ;
-  const unsigned nb = (unsigned)(g.half >> logLp) - 1u;
+__device__ __forceinline__ void pass_fwd_ot(float* sm, const Geo& g, int logLp, const float* __restrict__ ctab) {
+  const int logQ = logLp - 2, Q = 1 << logQ;
+  const unsigned nb = nodes_at(g, logLp);
   const unsigned Wr = nb << logQ, W = Wr * (unsigned)g.nreg;
   const Div dv(Wr);
-  const float* __restrict__ ct = ctab + (H - 2);
   for (unsigned w = threadIdx.x; w < W; w += TPB) {
     const unsigned r = dv(w), rem = w - r * Wr;
-    const int b = (int)(rem >> logQ), j = (int)(rem & (Q - 1)), j2 = H - 1 - j;
-    float* R = sm + r * g.RS;
-    const int p0 = b << logLp;
-    const int ctx = node_ctx<V>(p0, logLp, g.half, ctx_of(g, r));
-    const int pa = sw(p0 + j), pb = sw(p0 + H + j), pc = sw(p0 + j2), pd = sw(p0 + Lp - 1 - j);
-    const float c0 = __ldg(ct + j), c1 = __ldg(ct + j2);
-    if (ctx == 0) {
-      const float e0 = R[pa], o0 = R[pb] * c0, e1 = R[pc], o1 = R[pd] * c1;
-      R[pa] = e0 + o0; R[pd] = e0 - o0;
-      R[pc] = e1 + o1; R[pb] = e1 - o1;
-    } else {
-      const float o0 = R[pa] * c0, e0 = R[pb], o1 = R[pc] * c1, e1 = R[pd];
-      R[pa] = o0 + e0; R[pd] = o0 - e0;
-      R[pc] = o1 + e1; R[pb] = o1 - e1;
-    }
+    const int p0 = (int)(rem >> logQ) << logLp;
+    fwd_ot_quartet<V>(sm + r * g.RS, p0, logLp, node_ctx_g<V>(g, p0, logLp, ctx_of(g, r)), (int)(rem & (Q - 1)),
+                      ctab);
+  }
+}
+
+template <int V, int TPB>
+__device__ __forceinline__ void pass_bwd_to(float* sm, const Geo& g, int logLp, const float* __restrict__ ctab) {
+  const int logQ = logLp - 2, Q = 1 << logQ;
+  const unsigned nb = nodes_at(g, logLp);
+  const unsigned Wr = nb << logQ, W = Wr * (unsigned)g.nreg;
+  const Div dv(Wr);
+  for (unsigned w = threadIdx.x; w < W; w += TPB) {
+    const unsigned r = dv(w), rem = w - r * Wr;
+    const int p0 = (int)(rem >> logQ) << logLp;
+    bwd_to_quartet<V>(sm + r * g.RS, p0, logLp, node_ctx_g<V>(g, p0, logLp, ctx_of(g, r)), (int)(rem & (Q - 1)),
+                      ctab);
   }
 }
 
@@ -585,7 +619,7 @@ __device__ __forceinline__ void pass_bwd_to(float* sm, const Geo& g, int logLp, 
 template <int V, int TPB, int MAXI>
 __device__ __forceinline__ void pass_neighbour(float* sm, const Geo& g, int logLp) {
   const int Lp = 1 << logLp, H = Lp >> 1, h = logLp - 1;
-  const unsigned nb = (unsigned)(g.half >> logLp) - 1u;
+  const unsigned nb = nodes_at(g, logLp);
   const unsigned Wr = nb << h, W = Wr * (unsigned)g.nreg;
   const Div dv(Wr);
   float val[MAXI];
@@ -597,7 +631,7 @@ __device__ __forceinline__ void pass_neighbour(float* sm, const Geo& g, int logL
       const int b = (int)(rem >> h), q = (int)(rem & (H - 1)), i = brev(q, h);
       const float* R = sm + r * g.RS;
       const int p0 = b << logLp;
-      const int ctx = node_ctx<V>(p0, logLp, g.half, ctx_of(g, r));
+      const int ctx = node_ctx_g<V>(g, p0, logLp, ctx_of(g, r));
       const int base = ctx == 0 ? p0 + H : p0;
       const float bi = R[sw(base + q)];
       float o = bi;
@@ -626,7 +660,7 @@ __device__ __forceinline__ void pass_neighbour(float* sm, const Geo& g, int logL
       const int b = (int)(rem >> h), q = (int)(rem & (H - 1));
       float* R = sm + r * g.RS;
       const int p0 = b << logLp;
-      const int ctx = node_ctx<V>(p0, logLp, g.half, ctx_of(g, r));
+      const int ctx = node_ctx_g<V>(g, p0, logLp, ctx_of(g, r));
       const int base = ctx == 0 ? p0 + H : p0;
       R[sw(base + q)] = val[s];
     }
@@ -683,7 +717,7 @@ __device__ __forceinline__ void pass_recurrence(float* sm, float* tot, float* ws
   constexpr bool hstart = Var<V>::ot;
   constexpr bool alt = (V == 1 || V == 3);
   const int Lp = 1 << logLp, H = Lp >> 1, h = logLp - 1;
-  const unsigned nb = (unsigned)(g.half >> logLp) - 1u;
+  const unsigned nb = nodes_at(g, logLp);
   const unsigned total = nb * (unsigned)H * (unsigned)g.nreg;
   int logC = 1;
   while (((unsigned)TPB << logC) < total) ++logC;
@@ -700,7 +734,7 @@ __device__ __forceinline__ void pass_recurrence(float* sm, float* tot, float* ws
     const unsigned r = dv((unsigned)seg), b = (unsigned)seg - r * nb;
     R = sm + r * g.RS;
     const int p0 = (int)(b << logLp);
-    const int ctx = node_ctx<V>(p0, logLp, g.half, ctx_of(g, r));
+    const int ctx = node_ctx_g<V>(g, p0, logLp, ctx_of(g, r));
     base = ctx == 0 ? p0 + H : p0;
     if constexpr (V == 1) prefix = ctx == 0;
     else if constexpr (V == 5) prefix = ctx == 1;

@@ -1,9 +1,12 @@
 // Fused AM-QFT kernels of variant 8 (instantiated in a translation unit of
 // their own so the eight variants compile in parallel).
-#include "amqft_fused_impl.cuh"
+#include "amqft_multipass_impl.cuh"
 
 namespace amqft {
 cudaError_t launch_variant_8(const FusedArgs& a, const SmallConsts& K, const FusedConfig& c, cudaStream_t st) {
   return launch_v<8>(a, K, c, st);
+}
+cudaError_t multipass_variant_8(const MpArgs& a, float* W0, float* W1, const SmallConsts& K, cudaStream_t st) {
+  return mp_run<8>(a, W0, W1, K, st);
 }
 }  // namespace amqft

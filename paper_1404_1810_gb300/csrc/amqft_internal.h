@@ -7,6 +7,7 @@ namespace amqft {
 
 struct FusedArgs;
 struct SmallConsts;
+struct MpArgs;
 
 // Launch shape of the fused kernel for one transform length.
 struct FusedConfig {
@@ -29,5 +30,11 @@ cudaError_t launch_variant_5(const FusedArgs&, const SmallConsts&, const FusedCo
 cudaError_t launch_variant_6(const FusedArgs&, const SmallConsts&, const FusedConfig&, cudaStream_t);
 cudaError_t launch_variant_7(const FusedArgs&, const SmallConsts&, const FusedConfig&, cudaStream_t);
 cudaError_t launch_variant_8(const FusedArgs&, const SmallConsts&, const FusedConfig&, cudaStream_t);
+
+// multi-pass path (2^17 <= N <= 2^24), variants 2, 4, 6, 8
+cudaError_t multipass_variant_2(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t);
+cudaError_t multipass_variant_4(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t);
+cudaError_t multipass_variant_6(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t);
+cudaError_t multipass_variant_8(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t);
 
 }  // namespace amqft

@@ -1,0 +1,378 @@
+// Multi-pass AM-QFT for 2^17 <= N <= 2^24: the same recursion and the same
+// float32 operations as the fused kernel, with the four regions of each
+// transform held in a global workspace (same chain layout and swizzle).
+//
+//   load     D_c, D_r (and the first D_k for the harmonics-first variants),
+//            scattered into the regions;
+//   levels   tree levels of node size > S and chain levels of periodisation
+//            > 4S, one kernel per level: in-place quartets for the D_k time
+//            phase (ot trees) and the D_n frequency phase (to trees), gather
+//            form with a second workspace for the others;
+//   solve    one CTA per pair of tree nodes of size S (node mode) and one per
+//            region tail (the trees of size <= S plus the chain up to 4S, a
+//            region of N' = 4S) in shared memory, with the fused kernel's
+//            bands, register subtrees and passes;
+//   store    last chain level (time-first variants), D_r^F and D_c^F.
+//
+// Variants 2, 4, 6 and 8 only: the recurrences of 1, 3, 5 and 7 would need a
+// grid-wide scan per level.
+#pragma once
+
+#include "amqft_bands.cuh"
+#include "amqft_fused_impl.cuh"
+
+namespace amqft {
+
+constexpr int MP_LOG_S = 13;           // subproblem node size S = 2^13
+constexpr int MP_S = 1 << MP_LOG_S;
+constexpr int MP_TPB = 512;            // solve CTA: 16384 values, 32 per thread
+
+struct MpArgs {
+  const float2* in;
+  float2* out;
+  const float* ctab;
+  long long nt;       // transforms in this chunk
+  long long t0;       // first transform of the chunk (for in/out)
+  int logN;
+  int inverse;
+  long long RSg;      // region stride in the workspace (floats)
+};
+
+struct GRegions {
+  float* W;
+  long long RSg;
+  __device__ __forceinline__ float* get(long long t, int kind) const { return W + (t * 4 + kind) * RSg; }
+};
+
+template <int V>
+__global__ void mp_load_kernel(MpArgs a, float* W) {
+  const int logQ = a.logN - 2;
+  const long long total = a.nt << logQ;
+  const float cj = a.inverse ? -1.f : 1.f;
+  GRegions rg{W, a.RSg};
+  for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
+    const long long t = w >> logQ;
+    const int n = (int)(w & ((1LL << logQ) - 1));
+    const Fetched f = load_fetch(a.in, a.logN, a.t0 + t, n, cj);
+    load_scatter<V>(rg, a.logN, (int)t, n, f);
+  }
+}
+
+template <int V>
+__global__ void mp_store_kernel(MpArgs a, const float* W) {
+  const int logQ = a.logN - 2;
+  const long long total = a.nt << logQ;
+  const float cj = a.inverse ? -1.f : 1.f;
+  GRegions rg{const_cast<float*>(W), a.RSg};
+  for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
+    const long long t = w >> logQ;
+    const int k = (int)(w & ((1LL << logQ) - 1));
+    const Gathered g = store_gather<V>(rg, a.logN, (int)t, k);
+    store_emit<V>(a.out, a.logN, a.t0 + t, k, g, cj);
+  }
+}
+
+// in-place quartet level over every region (fwd: ot D_k time phase; else to
+// D_n frequency phase) at node size 2^logLp
+template <int V, bool FWD>
+__global__ void mp_quartet_kernel(MpArgs a, float* W, int logLp) {
+  const int half = 1 << (a.logN - 1), logQ = logLp - 2;
+  const long long nb = (half >> logLp) - 1;
+  const long long per = nb << logQ;
+  const long long total = per * 4 * a.nt;
+  for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
+    const long long rr = w / per, rem = w - rr * per;
+    float* R = W + rr * a.RSg;
+    const int ctx0 = (int)(rr & 1);
+    const int p0 = (int)(rem >> logQ) << logLp, i = (int)(rem & ((1 << logQ) - 1));
+    const int ctx = node_ctx<V>(p0, logLp, half, ctx0);
+    if constexpr (FWD) fwd_ot_quartet<V>(R, p0, logLp, ctx, i, a.ctab);
+    else bwd_to_quartet<V>(R, p0, logLp, ctx, i, a.ctab);
+  }
+}
+
+// Neighbour form of M_v on the B halves at node size 2^logLp (M4/M8
+// frequency phase, M2/M6 time phase), gather form Win -> Wout; every other
+// word is copied.
+template <int V>
+__global__ void mp_neighbour_kernel(MpArgs a, const float* __restrict__ Win, float* __restrict__ Wout, int logLp) {
+  const int half = 1 << (a.logN - 1), Lp = 1 << logLp, H = Lp >> 1, h = logLp - 1;
+  const long long total = a.RSg * 4 * a.nt;
+  for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
+    const long long rr = w / a.RSg;
+    const int ph = (int)(w - rr * a.RSg);  // physical (swizzled) word
+    const int p = sw(ph);                  // logical position (sw is an involution)
+    const float* R = Win + rr * a.RSg;
+    float v = R[ph];
+    if (p < half - Lp) {
+      const int p0 = p & ~(Lp - 1), qn = p - p0;
+      const int ctx = node_ctx<V>(p0, logLp, half, (int)(rr & 1));
+      const int base = ctx == 0 ? p0 + H : p0;
+      if (p >= base && p < base + H) {
+        const int q = p - base, i = brev(q, h);
+        int dir;
+        bool add;
+        if constexpr (V == 4) { dir = ctx == 0 ? +1 : -1; add = true; }
+        else if constexpr (V == 8) { dir = ctx == 0 ? -1 : +1; add = false; }
+        else if constexpr (V == 2) { dir = ctx == 0 ? -1 : +1; add = true; }
+        else { dir = ctx == 0 ? +1 : -1; add = false; }
+        const int jn = i + dir;
+        if (jn >= 0 && jn < H) {
+          const float bn = R[sw(base + brev(jn, h))];
+          v = add ? ((dir > 0) ? (v + bn) : (bn + v)) : (v - bn);
+        }
+        (void)qn;
+      }
+    }
+    Wout[rr * a.RSg + ph] = v;
+  }
+}
+
+// One chain level of periodisation M = 2^logM, gather form: ot variants the
+// D_n frequency phase, to variants the D_k time phase (Sect. 6.9).
+template <int V>
+__global__ void mp_chain_kernel(MpArgs a, const float* __restrict__ Win, float* __restrict__ Wout, int logM) {
+  const int half = 1 << (a.logN - 1), M = 1 << logM, logQ = logM - 2, Q = 1 << logQ, P = half - M / 2;
+  const long long total = a.RSg * 4 * a.nt;
+  for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
+    const long long rr = w / a.RSg;
+    const int ph = (int)(w - rr * a.RSg);
+    const int p = sw(ph);
+    const float* R = Win + rr * a.RSg;
+    const int ctx0 = (int)(rr & 1);
+    float v = R[ph];
+    const int rel = p - P;
+    if constexpr (Var<V>::ot) {
+      if (ctx0 == 0 && rel >= 0 && rel <= M / 2) {
+        if (rel == Q) {
+          v = R[sw(P + 2 * Q)];
+        } else {
+          const int k = rel < Q ? rel : M / 2 - rel;
+          const float e = R[sw(P + Q + k)], o = R[sw(P + brev(k, logQ))];
+          v = rel < Q ? (e + o) : (e - o);
+        }
+      } else if (ctx0 == 1 && rel >= 0 && rel < M / 2 - 1) {
+        const int k = rel + 1;
+        if (k == Q) {
+          v = R[sw(P + Q - 1)];
+        } else {
+          const int kk = k < Q ? k : M / 2 - k;
+          const float o = R[sw(P + brev(kk - 1, logQ))], e = R[sw(P + Q + kk - 1)];
+          v = k < Q ? (o + e) : (o - e);
+        }
+      }
+    } else {
+      if (ctx0 == 0 && rel >= 0 && rel <= M / 2) {
+        if (rel < Q) {
+          const int n = brev(rel, logQ);
+          v = R[sw(P + n)] - R[sw(P + M / 2 - n)];
+        } else {
+          const int n = rel - Q;
+          v = n < Q ? (R[sw(P + n)] + R[sw(P + M / 2 - n)]) : R[sw(P + Q)];
+        }
+      } else if (ctx0 == 1 && rel >= 0 && rel < M / 2 - 1) {
+        if (rel < Q) {
+          const int n = brev(rel, logQ) + 1;
+          v = n < Q ? (R[sw(P + n - 1)] + R[sw(P + M / 2 - n - 1)]) : R[sw(P + Q - 1)];
+        } else {
+          const int n = rel - Q + 1;
+          v = R[sw(P + n - 1)] - R[sw(P + M / 2 - n - 1)];
+        }
+      }
+    }
+    Wout[rr * a.RSg + ph] = v;
+  }
+}
+
+// Subproblem solve.  Blocks [0, nnode/2) of each region take two tree nodes
+// of size S each (node mode), the last block the region tail (region mode,
+// N' = 4S).  The words are copied verbatim: S and half - 2S are multiples of
+// 1024, so the swizzle of the workspace and of shared memory coincide.
+template <int V, int TPB>
+__global__ void __launch_bounds__(TPB) mp_solve_kernel(MpArgs a, float* W, const __grid_constant__ SmallConsts K) {
+  extern __shared__ __align__(16) float sm[];
+  const int half = 1 << (a.logN - 1);
+  const int nnode = (half >> MP_LOG_S) - 2;  // nodes of size S in [0, half - 2S)
+  const int per = nnode / 2 + 1;
+  const long long rr = blockIdx.x / per;
+  const int sidx = (int)(blockIdx.x - rr * per);
+  float* R = W + rr * a.RSg;
+  const int ctx0 = (int)(rr & 1);
+  const int RSn = MP_S + 32;
+  float* tot = sm + 2 * RSn + 64;  // scratch after the largest layout (tail: 2S + 32 words)
+  float* wsum = tot + TPB;
+  float* snap = wsum + 32;
+  Geo g;
+  if (sidx < nnode / 2) {
+    // node mode: nodes 2*sidx and 2*sidx + 1
+    const int n0 = 2 * sidx;
+    int mask = 0;
+    for (int j = 0; j < 2; ++j) {
+      const int p0 = (n0 + j) << MP_LOG_S;
+      mask |= node_ctx<V>(p0, MP_LOG_S, half, ctx0) << j;
+      for (int e = threadIdx.x; e < MP_S; e += TPB) sm[j * RSn + e] = R[p0 + e];
+    }
+    g.logN = MP_LOG_S + 2;
+    g.half = MP_S;
+    g.RS = RSn;
+    g.nreg = 2;
+    g.gbase = mask;
+    g.sub = MP_S;
+    __syncthreads();
+    const BandPlan bp = band_plan(MP_LOG_S + 2);
+    const int nleaf = MP_S >> LOG_LEAF;
+    if constexpr (Var<V>::ot) {
+      for (int b = 0; b < bp.nb; ++b) {
+        run_fold_band_r<V, TPB>(sm, g, bp.logL[b], bp.R[b], true, a.ctab);
+        __syncthreads();
+      }
+      for (int w = threadIdx.x; w < 2 * nleaf; w += TPB) {
+        const int r = w / nleaf, p0 = (w - r * nleaf) << LOG_LEAF;
+        run_leaf<V>(sm + r * RSn, p0, node_ctx_g<V>(g, p0, LOG_LEAF, ctx_of(g, r)), K);
+      }
+      __syncthreads();
+      for (int b = bp.nb - 1; b >= 0; --b) {
+        run_chunk_band_r<V, TPB>(sm, snap, g, bp.logL[b], bp.R[b]);
+        __syncthreads();
+      }
+    } else {
+      for (int lp = MP_LOG_S; lp >= LOG_LEAF + 1; --lp) {
+        pass_neighbour<V, TPB, 16>(sm, g, lp);
+        __syncthreads();
+      }
+      for (int w = threadIdx.x; w < 2 * nleaf; w += TPB) {
+        const int r = w / nleaf, p0 = (w - r * nleaf) << LOG_LEAF;
+        run_leaf<V>(sm + r * RSn, p0, node_ctx_g<V>(g, p0, LOG_LEAF, ctx_of(g, r)), K);
+      }
+      __syncthreads();
+      for (int b = bp.nb - 1; b >= 0; --b) {
+        run_fold_band_r<V, TPB>(sm, g, bp.logL[b], bp.R[b], false, a.ctab);
+        __syncthreads();
+      }
+    }
+    for (int j = 0; j < 2; ++j) {
+      const int p0 = (n0 + j) << MP_LOG_S;
+      for (int e = threadIdx.x; e < MP_S; e += TPB) R[p0 + e] = sm[j * RSn + e];
+    }
+  } else {
+    // tail: region of N' = 4S at [half - 2S, RSg)
+    const int base = half - 2 * MP_S;
+    const int words = (int)a.RSg - base;
+    for (int e = threadIdx.x; e < words; e += TPB) sm[e] = R[base + e];
+    const int logNp = MP_LOG_S + 2, halfp = 2 * MP_S;
+    g.logN = logNp;
+    g.half = halfp;
+    g.RS = words;
+    g.nreg = 1;
+    g.gbase = ctx0;
+    g.sub = 0;
+    __syncthreads();
+    const BandPlan bp = band_plan(logNp);
+    const int nleaf = (halfp >> LOG_LEAF) - 1;
+    if constexpr (Var<V>::ot) {
+      for (int b = 0; b < bp.nb; ++b) {
+        run_fold_band_r<V, TPB>(sm, g, bp.logL[b], bp.R[b], true, a.ctab);
+        __syncthreads();
+      }
+      for (int w = threadIdx.x; w < nleaf + 1; w += TPB) {
+        if (w < nleaf) run_leaf<V>(sm, w << LOG_LEAF, node_ctx_g<V>(g, w << LOG_LEAF, LOG_LEAF, ctx0), K);
+        else run_tail<V>(sm, ctx0, logNp, K);
+      }
+      __syncthreads();
+      for (int b = bp.nb - 1; b >= 0; --b) {
+        run_chunk_band_r<V, TPB>(sm, snap, g, bp.logL[b], bp.R[b]);
+        __syncthreads();
+      }
+      for (int lm = LOG_LEAF + 2; lm <= logNp; ++lm) {
+        pass_chain<V, TPB, 32>(sm, g, lm);
+        __syncthreads();
+      }
+    } else {
+      for (int lm = logNp; lm >= LOG_LEAF + 2; --lm) {
+        pass_chain<V, TPB, 32>(sm, g, lm);
+        __syncthreads();
+      }
+      if (threadIdx.x == 0) run_tail<V>(sm, ctx0, logNp, K);
+      __syncthreads();
+      for (int lp = logNp - 2; lp >= LOG_LEAF + 1; --lp) {
+        pass_neighbour<V, TPB, 16>(sm, g, lp);
+        __syncthreads();
+      }
+      for (int w = threadIdx.x; w < nleaf; w += TPB)
+        run_leaf<V>(sm, w << LOG_LEAF, node_ctx_g<V>(g, w << LOG_LEAF, LOG_LEAF, ctx0), K);
+      __syncthreads();
+      for (int b = bp.nb - 1; b >= 0; --b) {
+        run_fold_band_r<V, TPB>(sm, g, bp.logL[b], bp.R[b], false, a.ctab);
+        __syncthreads();
+      }
+    }
+    for (int e = threadIdx.x; e < words; e += TPB) R[base + e] = sm[e];
+  }
+}
+
+inline int mp_solve_smem_bytes() {
+  // tail layout (2S + 32 words) is the larger one; then scan scratch and snapshot
+  return (2 * (MP_S + 32) + 64 + MP_TPB + 32 + snap_floats(2 * MP_S)) * (int)sizeof(float);
+}
+
+// Host side: the whole sequence for one chunk of transforms.
+template <int V>
+cudaError_t mp_run(const MpArgs& a0, float* W0, float* W1, const SmallConsts& K, cudaStream_t st) {
+  MpArgs a = a0;
+  const int logN = a.logN, N = 1 << logN;
+  const int threads = 256;
+  auto grid_for = [&](long long items) {
+    long long b = (items + threads - 1) / threads;
+    return (unsigned)(b < 152LL * 32 ? (b > 0 ? b : 1) : 152LL * 32);
+  };
+  cudaError_t e;
+  float* cur = W0;
+  float* oth = W1;
+  const long long words = a.RSg * 4 * a.nt;
+  mp_load_kernel<V><<<grid_for(a.nt * (N / 4)), threads, 0, st>>>(a, cur);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const int smem = mp_solve_smem_bytes();
+  e = cudaFuncSetAttribute(mp_solve_kernel<V, MP_TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const int half = N / 2;
+  const unsigned nsolve = (unsigned)(4 * a.nt * ((half >> MP_LOG_S) / 2));  // nnode/2 + 1 per region
+  if constexpr (Var<V>::ot) {
+    for (int lp = logN - 2; lp >= MP_LOG_S + 1; --lp) {
+      mp_quartet_kernel<V, true><<<grid_for(4 * a.nt * (half >> 2)), threads, 0, st>>>(a, cur, lp);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    mp_solve_kernel<V, MP_TPB><<<nsolve, MP_TPB, smem, st>>>(a, cur, K);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    for (int lp = MP_LOG_S + 1; lp <= logN - 2; ++lp) {
+      mp_neighbour_kernel<V><<<grid_for(words), threads, 0, st>>>(a, cur, oth, lp);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      float* t = cur; cur = oth; oth = t;
+    }
+    for (int lm = MP_LOG_S + 3; lm <= logN - 1; ++lm) {
+      mp_chain_kernel<V><<<grid_for(words), threads, 0, st>>>(a, cur, oth, lm);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      float* t = cur; cur = oth; oth = t;
+    }
+  } else {
+    for (int lm = logN - 1; lm >= MP_LOG_S + 3; --lm) {
+      mp_chain_kernel<V><<<grid_for(words), threads, 0, st>>>(a, cur, oth, lm);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      float* t = cur; cur = oth; oth = t;
+    }
+    for (int lp = logN - 2; lp >= MP_LOG_S + 1; --lp) {
+      mp_neighbour_kernel<V><<<grid_for(words), threads, 0, st>>>(a, cur, oth, lp);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      float* t = cur; cur = oth; oth = t;
+    }
+    mp_solve_kernel<V, MP_TPB><<<nsolve, MP_TPB, smem, st>>>(a, cur, K);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    for (int lp = MP_LOG_S + 1; lp <= logN - 2; ++lp) {
+      mp_quartet_kernel<V, false><<<grid_for(4 * a.nt * (half >> 2)), threads, 0, st>>>(a, cur, lp);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+  }
+  mp_store_kernel<V><<<grid_for(a.nt * (N / 4)), threads, 0, st>>>(a, cur);
+  return cudaGetLastError();
+}
+
+}  // namespace amqft

@@ -1,0 +1,102 @@
+"""Multi-pass path (2^17 <= N <= 2^24, variants 2, 4, 6, 8) against the oracle.
+
+The passes perform the same float32 operations as the recursion, so the
+results must be bit-identical to the oracle's float32 instantiation where the
+oracle can run (up to 2^20 here); at 2^24, beyond the oracle's reach in a
+test, sampled bins of the DFT definition, Parseval and the inverse pin it.
+"""
+import numpy as np
+import pytest
+
+import synth
+from gpu_util import derived_tol, rel, run_gpu
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def lib():
+    import torch
+
+    from paper_1404_1810_gb300 import build, load
+
+    assert torch.cuda.is_available()
+    build.build()
+    return load()
+
+
+@pytest.mark.parametrize("v", [4, 2, 8, 6])
+@pytest.mark.parametrize("log2n", [17, 18])
+def test_multipass_bitexact(orc, v, log2n):
+    n = 1 << log2n
+    x = synth.normal_complex(n, 3, config=2, stream=500 + log2n)
+    for inverse in (False, True):
+        y = run_gpu(x, v, inverse=inverse)
+        row = 2
+        xr = x[row].astype(np.complex64).astype(np.complex128)
+        r32 = orc.amqft(xr, v, prec="f32", sign=+1 if inverse else -1)
+        assert np.array_equal(y[row].astype(np.complex64), r32.astype(np.complex64)), (v, log2n, inverse)
+        if v in (2, 4):
+            r64 = orc.amqft(xr, v, sign=+1 if inverse else -1)
+            assert rel(y[row], r64) <= derived_tol(rel(r32, r64), log2n)
+
+
+@pytest.mark.parametrize("v", [4, 2])
+def test_multipass_2pow20(orc, v):
+    n = 1 << 20
+    x = synth.normal_complex(n, 2, config=2, stream=520)
+    y = run_gpu(x, v)
+    xr = x[1].astype(np.complex64).astype(np.complex128)
+    r32 = orc.amqft(xr, v, prec="f32")
+    assert np.array_equal(y[1].astype(np.complex64), r32.astype(np.complex64))
+
+
+def dft_bins(x, ks):
+    """The DFT definition (Eq. qft_0A) at a few bins, float64, angles reduced exactly."""
+    n = len(x)
+    idx = np.arange(n, dtype=np.int64)
+    out = []
+    for k in ks:
+        ph = np.mod(idx * int(k), n).astype(np.float64) / n
+        out.append(np.sum(x * np.exp(-2j * np.pi * ph)))
+    return np.array(out)
+
+
+@pytest.mark.parametrize("v", [4, 2])
+def test_multipass_2pow24_properties(v):
+    n = 1 << 24
+    x = synth.normal_complex(n, 1, config=2, stream=524).astype(np.complex64).astype(np.complex128)
+    y = run_gpu(x, v)[0]
+    # sampled bins against the definition; the float32 recursion's error at
+    # 2^24 is about 1.6e-4 relative (it grows like sqrt(N)), per-bin scale sqrt(N)
+    ks = [0, 1, 2, 3, 5, n // 4, n // 2 - 1, n // 2, n // 2 + 1, n - 1, 123457, 9876543]
+    ref = dft_bins(x[0], ks)
+    err = np.abs(y[ks] - ref) / np.sqrt(n)
+    assert np.max(err) < 2e-3, err
+    # Parseval
+    e_in = np.sum(np.abs(x[0]) ** 2)
+    assert abs(np.sum(np.abs(y) ** 2) / (n * e_in) - 1.0) < 1e-4
+    # inverse(forward) = N x
+    z = run_gpu(y[None, :], v, inverse=True)[0]
+    assert rel(z, n * x[0]) < 1e-3
+
+
+def test_multipass_chunked_batch(orc):
+    """2^24 with a batch larger than one workspace chunk (8 transforms)."""
+    n, b = 1 << 24, 9
+    import torch
+
+    from paper_1404_1810_gb300 import Plan
+
+    x = synth.device_normal_complex64(n, b, "cuda")
+    p = Plan(24, 4, b)
+    y = p.fwd(x)
+    torch.cuda.synchronize()
+    p.close()
+    # the last transform (second chunk) must equal a batch-1 run of the same data
+    p1 = Plan(24, 4, 1)
+    y1 = p1.fwd(x[b - 1:b].contiguous())
+    torch.cuda.synchronize()
+    p1.close()
+    assert torch.equal(y[b - 1], y1[0])
+    assert torch.isfinite(y).all()

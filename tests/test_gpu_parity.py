@@ -162,8 +162,11 @@ def test_empty_batch_and_errors():
         amqft_plan(10, 9, 1)
     assert e.value.code == -2
     with pytest.raises(AmqftError) as e:
-        amqft_plan(17, 4, 1)
+        amqft_plan(25, 4, 1)
     assert e.value.code == -1
+    with pytest.raises(AmqftError) as e:          # recurrence variants stop at 2^16
+        amqft_plan(17, 1, 1)
+    assert e.value.code == -2
     with pytest.raises(AmqftError) as e:
         amqft_plan(10, 4, 1, 7)
     assert e.value.code == -3

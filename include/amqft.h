@@ -93,6 +93,41 @@ const char *amqft_version(void);
  * Any out pointer may be NULL. */
 int amqft_plan_info(amqft_plan_t plan, int *cluster, int *per_cta, int *threads, int *smem_bytes);
 
+/* ---------------------------------------------------------------------
+ * Allocation-free execution.  The paper has no counterpart to this entry
+ * point: it runs the same multi-pass kernels as amqft_exec_fwd/inv, with
+ * their workspace in a fixed device array compiled into the library instead
+ * of one the plan allocates.  It serves callers that must not allocate device
+ * memory when they run a transform (cudaMalloc/cudaFree may synchronise the
+ * device or fail when another allocator owns the free memory) and callers
+ * that cannot keep a workspace per plan.
+ */
+#define AMQFT_STATIC_LOG2N_MIN 17
+#define AMQFT_STATIC_LOG2N_MAX 20
+/* 2 transforms x 2 ping-pong buffers x 4 regions x (2^19 + 32) floats:
+ * 32 MiB + 2 KiB per device, reserved when the library's module is loaded. */
+#define AMQFT_STATIC_SCRATCH_FLOATS 8389120LL
+
+/* Run `batch` transforms of the plan's length and variant: forward
+ * (inverse == 0, out = DFT(in)) or unnormalised inverse (inverse != 0,
+ * out = conj(DFT(conj(in)))), bit-identical to amqft_exec_fwd/inv of a plan
+ * with that batch.  The plan supplies length, variant and constant table and
+ * its own batch is ignored: create it with batch 0 so that it holds no
+ * workspace.  in/out: device pointers to batch * 2^log2n interleaved complex
+ * float32 values, owned by the caller, 8-byte aligned, not overlapping.
+ * Makes no device or host allocation.  The first call on a device looks up
+ * the scratch array's address (and so may load the library's module into the
+ * context); make it before any stream capture.  The scratch is shared by
+ * every plan on the device: calls that overlap in time (different streams, or
+ * host threads without ordering) race; calls on one stream are ordered.
+ * Nothing in the scratch needs to start at zero.
+ * Errors: AMQFT_ERR_ARG (NULL plan, batch < 0), AMQFT_ERR_N (plan length
+ * outside [2^AMQFT_STATIC_LOG2N_MIN, 2^AMQFT_STATIC_LOG2N_MAX]: shorter
+ * lengths use no workspace, longer ones need more than the array holds),
+ * AMQFT_ERR_DTYPE, AMQFT_ERR_ALIGN, AMQFT_ERR_INPLACE, AMQFT_ERR_DEVICE (the
+ * current device is not the plan's), AMQFT_ERR_CUDA. */
+int amqft_exec_static(amqft_plan_t plan, int64_t batch, const void *in, void *out, int inverse, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -51,6 +51,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.amqft_destroy.restype = i32
         lib.amqft_last_error.restype = ctypes.c_char_p
         lib.amqft_version.restype = ctypes.c_char_p
+        lib.amqft_exec_static.argtypes = [vp, i64, vp, vp, i32, vp]
+        lib.amqft_exec_static.restype = i32
         lib.amqft_plan_info.argtypes = [vp] + [ctypes.POINTER(i32)] * 4
         lib.amqft_plan_info.restype = i32
         _lib = lib
@@ -77,6 +79,13 @@ def amqft_exec_fwd(plan: int, d_in: int, d_out: int, exp_out: int = 0, stream: i
 def amqft_exec_inv(plan: int, d_in: int, exp_in: int, d_out: int, exp_out: int = 0, stream: int = 0) -> None:
     _check(load().amqft_exec_inv(plan, d_in, exp_in or None, d_out, exp_out or None, stream or None),
            "amqft_exec_inv")
+
+
+def amqft_exec_static(plan: int, batch: int, d_in: int, d_out: int, inverse: int = 0, stream: int = 0) -> None:
+    """Multi-pass transform (2^17..2^20) with the library's fixed device scratch:
+    no allocation in the call; calls overlapping in time on one device race."""
+    _check(load().amqft_exec_static(plan, int(batch), d_in, d_out, int(inverse), stream or None),
+           "amqft_exec_static")
 
 
 def amqft_destroy(plan: int) -> None:

@@ -147,6 +147,33 @@ struct amqft_plan_s {
 // workspace budget of one plan (both ping-pong buffers)
 static const long long kWorkspaceBytes = 2LL << 30;
 
+namespace amqft {
+
+int plan_view(amqft_plan_t p, PlanView* v) {
+  if (!p || !v) return fail(AMQFT_ERR_ARG, "plan is NULL");
+  v->log2n = p->log2n;
+  v->variant = p->variant;
+  v->dtype = p->dtype;
+  v->device = p->device;
+  v->ctab = p->d_ctab;
+  v->small = &p->small;
+  return AMQFT_OK;
+}
+
+int set_error(int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return code;
+}
+
+void clear_error() { t_err.clear(); }
+
+}  // namespace amqft
+
 extern "C" {
 
 const char* amqft_last_error(void) { return t_err.c_str(); }

@@ -3,6 +3,8 @@
 
 #include <cuda_runtime.h>
 
+#include "amqft.h"
+
 namespace amqft {
 
 struct FusedArgs;
@@ -36,5 +38,21 @@ cudaError_t multipass_variant_2(const MpArgs&, float*, float*, const SmallConsts
 cudaError_t multipass_variant_4(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t);
 cudaError_t multipass_variant_6(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t);
 cudaError_t multipass_variant_8(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t);
+
+// Read-only view of a plan, for entry points defined outside the plan's
+// translation unit.  Returns AMQFT_ERR_ARG for a NULL plan.
+struct PlanView {
+  int log2n;
+  int variant;
+  int dtype;
+  int device;                // device the plan's constant table lives on
+  const float* ctab;         // device constant table (NULL for N < 16)
+  const SmallConsts* small;  // host copy of the leaf constants
+};
+int plan_view(amqft_plan_t plan, PlanView* v);
+
+// Record the calling thread's error message (amqft_last_error) and return code.
+int set_error(int code, const char* fmt, ...);
+void clear_error();
 
 }  // namespace amqft

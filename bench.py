@@ -164,8 +164,9 @@ def cpu_baseline(x_host_rows, variant, sign_pair=True):
     _, threads = oracle.amqft_batch(x_host_rows[:1], variant, threads=1)
     t1 = time.perf_counter() - t0
     cores = os.cpu_count() or 1
-    # about 12 s of CPU work: S transforms forward + S inverse
-    s = max(cores, int(12.0 / max(2 * t1, 1e-3)) // cores * cores)
+    # about 12 s of wall time on all cores: S transforms forward + S inverse,
+    # one transform pair taking about 2 * t1 on each core
+    s = max(cores, int(12.0 * cores / max(2 * t1, 1e-3)) // cores * cores)
     s = min(s, x_host_rows.shape[0])
     rows = np.ascontiguousarray(x_host_rows[:s])
     t0 = time.perf_counter()

@@ -51,6 +51,10 @@ def parse_args():
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c1", "c3", "c5"],
+                    help="c2 (default): the batched complex64 forward+inverse line; c1: N=1024 latency of "
+                         "all variants; c3: 16-bit storage; c5: autograd forward+backward")
+    ap.add_argument("--dtype16", default="bf16", choices=["bf16", "fp16"])
     return ap.parse_args()
 
 
@@ -217,10 +221,201 @@ def run_reference(args):
     return 0
 
 
+def _event_steps(torch, stream, K, fns):
+    """Time K steps of the callables fns (each one launch group) with CUDA
+    events on `stream`; returns (total ms, mean ms of each callable)."""
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(fns) + 1)] for _ in range(K)]
+    torch.cuda.synchronize()
+    for i in range(K):
+        ev[i][0].record(stream)
+        for j, f in enumerate(fns):
+            f()
+            ev[i][j + 1].record(stream)
+    torch.cuda.synchronize()
+    total = ev[0][0].elapsed_time(ev[K - 1][len(fns)])
+    per = [statistics.mean(ev[i][j].elapsed_time(ev[i][j + 1]) for i in range(K)) for j in range(len(fns))]
+    return total, per
+
+
+def run_extra(args):
+    """The other configurations of the workload list, each as its own JSON
+    line, measured beside the plain float32 batched form on the same GPU."""
+    import numpy as np
+    import torch
+
+    import synth
+    from paper_1404_1810_gb300 import Plan, amqft_autograd, build, dequantize, load
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return 0
+    build.build()
+    load()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream()
+    peak, kind = measured_peak()
+    K, W = args.steps, max(args.warmup, 3)
+    sampler = ClockSampler(0)
+
+    def fp32_reference(log2n, batch):
+        n = 1 << log2n
+        x = synth.device_normal_complex64(n, batch, dev)
+        y, z = torch.empty_like(x), torch.empty_like(x)
+        p = Plan(log2n, args.variant, batch)
+        for _ in range(W):
+            p.fwd(x, y, stream)
+            p.inv(y, z, stream)
+        tot, per = _event_steps(torch, stream, K, [lambda: p.fwd(x, y, stream), lambda: p.inv(y, z, stream)])
+        p.close()
+        del x, y, z
+        return {"value": 2 * batch * n / (tot / K * 1e-3) / 1e9, "unit": UNIT, "fwd_kernel_ms": per[0],
+                "config": f"complex64 N=2^{log2n} x {batch}, variant {args.variant}"}
+
+    if args.workload == "c1":
+        import oracle
+
+        oracle.build()
+        n = 1024
+        x = synth.uniform_complex(n, 1, config=1)
+        truth = oracle.naive_dft(x[0].astype(np.complex64).astype(np.complex128))
+        xd = torch.from_numpy(x.astype(np.complex64)).to(dev)
+        res = {}
+        sampler.start()
+        for v in range(1, 9):
+            p = Plan(10, v, 1)
+            y = torch.empty_like(xd)
+            for _ in range(W):
+                p.fwd(xd, y, stream)
+            tot, per = _event_steps(torch, stream, K, [lambda: p.fwd(xd, y, stream)])
+            err = float(np.linalg.norm(y.cpu().numpy()[0] - truth) / np.linalg.norm(truth))
+            res[str(v)] = {"us_per_transform": 1e3 * per[0], "rel_l2_vs_long_double_dft": err}
+            p.close()
+        clocks = sampler.stop()
+        best = min(r["us_per_transform"] for r in res.values())
+        line = {"metric": "AM-QFT single complex DFT latency, N=1024, all 8 variants", "value": best, "unit": "us",
+                "higher_is_better": False, "n_gpus": 1, "steps": K, "warmup": W, "dtype": "f32",
+                "data": "synthetic", "config": {"workload": "single complex DFT N=1024, Re/Im iid U[-1,1)",
+                                                "batch": 1}, "per_variant": res, "clocks": clocks,
+                "gpu_launches": 8 * K, "vs_baseline": None, "impl": "amqft"}
+        print(json.dumps(line), flush=True)
+        return 0
+
+    if args.workload == "c3":
+        import oracle
+
+        oracle.build()
+        dt = 1 if args.dtype16 == "bf16" else 2
+        tdt = torch.bfloat16 if dt == 1 else torch.float16
+        log2n = args.log2n
+        n = 1 << log2n
+        batch = 1 << (27 - log2n)
+        x = torch.view_as_real(synth.device_normal_complex64(n, batch, dev)).to(tdt).contiguous()
+        y, z = torch.empty_like(x), torch.empty_like(x)
+        ey = torch.empty(batch, dtype=torch.int32, device=dev)
+        ez = torch.empty(batch, dtype=torch.int32, device=dev)
+        p = Plan(log2n, args.variant, batch, dt)
+        for _ in range(W):
+            p.fwd(x, y, stream, ey)
+            p.inv(y, z, stream, exp_in=ey, exp_out=ez)
+        sampler.start()
+        tot, per = _event_steps(torch, stream, K, [lambda: p.fwd(x, y, stream, ey),
+                                                   lambda: p.inv(y, z, stream, exp_in=ey, exp_out=ez)])
+        clocks = sampler.stop()
+        value = 2 * batch * n / (tot / K * 1e-3) / 1e9
+        achieved = 8 * batch * n / (per[0] * 1e-3) / 1e9
+        errs, maxe = [], []
+        for i in (0, batch - 1):
+            xin = torch.view_as_complex(x[i].double()).cpu().numpy()
+            r64 = oracle.amqft(xin, args.variant)
+            yi = dequantize(y[i:i + 1], ey[i:i + 1]).cpu().numpy()[0]
+            errs.append(float(np.linalg.norm(yi - r64) / np.linalg.norm(r64)))
+            maxe.append(float(np.max(np.abs(yi - r64)) / np.max(np.abs(r64))))
+        p.close()
+        del x, y, z
+        ref = fp32_reference(log2n, batch)
+        line = {"metric": f"AM-QFT {args.dtype16} storage / f32 compute, Gpoints/s", "value": value, "unit": UNIT,
+                "higher_is_better": True, "n_gpus": 1, "steps": K, "warmup": W, "dtype": f"{args.dtype16}-storage",
+                "data": "synthetic",
+                "config": {"workload": f"16-bit storage forward+inverse, N=2^{log2n}, batch {batch} (2^27 points), "
+                                       f"Re/Im iid N(0,1) rounded to {args.dtype16}", "variant": args.variant,
+                           "l2": "inputs larger than L2"},
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": None, "peak_kind": kind,
+                             "kernel_ms": per[0], "algorithmic_bytes_per_launch": 8 * batch * n},
+                "accuracy": {"rel_l2_vs_f64_oracle": max(errs), "max_abs_over_max": max(maxe), "tol": 4e-3,
+                             "sample": "transforms 0 and batch-1, oracle on the 16-bit input"},
+                "vs_fp32_same_gpu": ref, "clocks": clocks, "gpu_launches": 2 * K, "vs_baseline": None,
+                "impl": "amqft"}
+        print(json.dumps(line), flush=True)
+        return 0
+
+    # c5: autograd, 512 real signals of N = 2^14 lifted to complex
+    import oracle
+
+    oracle.build()
+    log2n, batch = 14, 512
+    n = 1 << log2n
+    g = torch.Generator(device=dev)
+    g.manual_seed(synth.SEED_BASE + 5)
+    xr = (torch.rand((batch, n), generator=g, device=dev) * 2 - 1).requires_grad_(True)
+    w = torch.rand((n,), generator=g, device=dev)
+    state = {}
+
+    def fwd():
+        z = torch.complex(xr, torch.zeros_like(xr))
+        X = amqft_autograd(z, args.variant)
+        state["loss"] = (w * (X.real ** 2 + X.imag ** 2)).sum()
+
+    def bwd():
+        xr.grad = None
+        state["loss"].backward()
+
+    for _ in range(W):
+        fwd()
+        bwd()
+    sampler.start()
+    tot, per = _event_steps(torch, stream, K, [fwd, bwd])
+    clocks = sampler.stop()
+    value = batch * n / (tot / K * 1e-3) / 1e9
+    # kernel-only: the two transforms of a step
+    p = Plan(log2n, args.variant, batch)
+    zc = torch.complex(xr.detach(), torch.zeros_like(xr.detach())).contiguous()
+    yk, gk = torch.empty_like(zc), torch.empty_like(zc)
+    for _ in range(W):
+        p.fwd(zc, yk, stream)
+        p.inv(yk, gk, stream)
+    ktot, kper = _event_steps(torch, stream, K, [lambda: p.fwd(zc, yk, stream), lambda: p.inv(yk, gk, stream)])
+    p.close()
+    achieved = 32 * batch * n / ((kper[0] + kper[1]) * 1e-3) / 1e9
+    x0 = xr.detach()[0].double().cpu().numpy().astype(np.complex128)
+    wn = w.double().cpu().numpy()
+    X0 = oracle.amqft(x0, args.variant)
+    gref = 2.0 * oracle.amqft(wn * X0, args.variant, sign=+1).real
+    gerr = float(np.linalg.norm(xr.grad[0].double().cpu().numpy() - gref) / np.linalg.norm(gref))
+    ref = fp32_reference(log2n, batch)
+    line = {"metric": "AM-QFT autograd forward+backward Gpoints/s", "value": value, "unit": UNIT,
+            "higher_is_better": True, "n_gpus": 1, "steps": K, "warmup": W, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "autograd: 512 real signals N=2^14 lifted to complex, loss = sum_k w_k |X_k|^2, "
+                                   "w ~ U[0,1); step = forward + backward", "variant": args.variant},
+            "step_ms": {"forward_incl_loss": per[0], "backward": per[1]},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": kind,
+                         "kernel_ms": {"forward": kper[0], "adjoint": kper[1]},
+                         "algorithmic_bytes": "32 B per point for the two transforms; mask and loss elementwise "
+                                              "ops excluded"},
+            "accuracy": {"grad_rel_l2_vs_oracle_adjoint": gerr, "sample": "signal 0, 2 Re F^H(w X), float64"},
+            "vs_fp32_same_gpu": ref, "clocks": clocks, "gpu_launches": 2 * K, "vs_baseline": None,
+            "impl": "amqft"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload != "c2":
+        return run_extra(args)
 
     import numpy as np
     import torch

@@ -13,6 +13,15 @@
  *   - Data are interleaved complex (re, im), transform-major: transform b
  *     occupies elements [b*N, (b+1)*N).  AMQFT_C64 elements are 2 x float32
  *     (8 bytes); in and out must be 8-byte aligned device pointers.
+ *   - 16-bit storage (AMQFT_CBF16, AMQFT_CF16): an element is a pair of
+ *     bfloat16 or IEEE binary16 values (4 bytes, real part first), in and out
+ *     4-byte aligned.  Transform b holds the values stored * 2^exp[b], one
+ *     int32 exponent per transform in a separate device array.  Arithmetic is
+ *     float32 throughout: inputs are widened and scaled exactly; each output
+ *     transform gets the exponent that puts its largest component magnitude
+ *     in [2^13, 2^14) (0 for an all-zero transform), is scaled by 2^-exp
+ *     exactly and rounded once to nearest even.  Exponents are clamped to
+ *     [-100, 100] (outside that range the scaling saturates).
  *   - in and out are owned by the caller; they must not overlap.
  *   - stream is a cudaStream_t (NULL = legacy default stream).  Calls are
  *     asynchronous on that stream and make no host synchronisation.
@@ -50,7 +59,7 @@ typedef enum { AMQFT_C64 = 0, AMQFT_CBF16 = 1, AMQFT_CF16 = 2 } amqft_dtype;
 typedef struct amqft_plan_s *amqft_plan_t;
 
 /* Create a plan for `batch` transforms of length 2^log2n with AM-QFT
- * variant `variant` (1..8, Sect. 6) and storage `dtype`.
+ * variant `variant` (1..8, Sect. 6) and storage `dtype` (amqft_dtype).
  * The plan owns the variant's trig-constant table (Sect. 7.1: the
  * M/8 constants 2cos, 1/(2cos), 2sin or 1/(2sin) of theta*(2j+1) for every
  * periodisation M = 16..N, N/4 - 2 floats in all) on the current device.
@@ -61,19 +70,22 @@ typedef struct amqft_plan_s *amqft_plan_t;
  * chunk, at most 2 GiB, the batch processed chunk by chunk.
  * Errors: AMQFT_ERR_N (log2n < 0 or > AMQFT_LOG2N_MAX), AMQFT_ERR_VARIANT
  * (also variants 1, 3, 5, 7 with log2n > AMQFT_LOG2N_FUSED_MAX),
- * AMQFT_ERR_DTYPE, AMQFT_ERR_ARG (out NULL or batch < 0), AMQFT_ERR_DEVICE,
+ * AMQFT_ERR_DTYPE (not an amqft_dtype), AMQFT_ERR_ARG (out NULL or batch < 0), AMQFT_ERR_DEVICE,
  * AMQFT_ERR_NOMEM, AMQFT_ERR_CUDA.  On error *out is set to NULL. */
 int amqft_plan(amqft_plan_t *out, int log2n, int variant, int64_t batch, int dtype);
 
 /* Forward transform of the plan's batch: out = DFT(in), Eq. qft_0A.
- * exp_out is reserved for 16-bit storage (per-transform exponents) and must
- * be NULL for AMQFT_C64.  Errors: AMQFT_ERR_ARG, AMQFT_ERR_ALIGN,
- * AMQFT_ERR_INPLACE, AMQFT_ERR_DTYPE, AMQFT_ERR_CUDA (launch failure). */
+ * exp_out: AMQFT_C64 plans, NULL; 16-bit plans, a device array of `batch`
+ * int32 that receives the output exponents (the input exponents are 0).
+ * Errors: AMQFT_ERR_ARG (NULL plan; exp_out NULL for 16-bit), AMQFT_ERR_ALIGN,
+ * AMQFT_ERR_INPLACE, AMQFT_ERR_DTYPE (exponents given for AMQFT_C64),
+ * AMQFT_ERR_CUDA (launch failure). */
 int amqft_exec_fwd(amqft_plan_t plan, const void *in, void *out, int32_t *exp_out, void *stream);
 
 /* Unnormalised inverse / adjoint: out = conj(DFT(conj(in))) = N * IDFT(in).
- * exp_in / exp_out are reserved for 16-bit storage and must be NULL for
- * AMQFT_C64.  Errors as amqft_exec_fwd. */
+ * exp_in / exp_out: NULL for AMQFT_C64; for 16-bit plans exp_in holds the
+ * input exponents (NULL: all 0) and exp_out receives the output exponents.
+ * Errors as amqft_exec_fwd. */
 int amqft_exec_inv(amqft_plan_t plan, const void *in, const int32_t *exp_in, void *out,
                    int32_t *exp_out, void *stream);
 

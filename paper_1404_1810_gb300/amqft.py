@@ -116,8 +116,17 @@ def _stream_handle(stream) -> int:
     return int(stream.cuda_stream)
 
 
+_TORCH_16 = {AMQFT_CBF16: "bfloat16", AMQFT_CF16: "float16"}
+
+
 class Plan:
-    """Owns one amqft plan; fwd/inv take complex64 CUDA tensors (batch, N)."""
+    """Owns one amqft plan.
+
+    complex64 plans: fwd/inv take and return contiguous complex64 CUDA
+    tensors of shape (batch, N).  16-bit plans (AMQFT_CBF16, AMQFT_CF16):
+    tensors of shape (batch, N, 2) in bfloat16 / float16 (real, imaginary),
+    plus one int32 exponent per transform: fwd(x) returns (y, exp_y) and
+    inv(x, exp_x) returns (y, exp_y), the values being y * 2^exp_y."""
 
     def __init__(self, log2n: int, variant: int, batch: int, dtype: int = AMQFT_C64):
         self.log2n, self.variant, self.batch, self.dtype = int(log2n), int(variant), int(batch), int(dtype)
@@ -130,30 +139,60 @@ class Plan:
     def _check_tensor(self, t, name):
         import torch
 
-        if t.dtype != torch.complex64 or not t.is_cuda or not t.is_contiguous():
-            raise ValueError(f"{name} must be a contiguous complex64 CUDA tensor")
-        if t.numel() != self.batch * self.n:
-            raise ValueError(f"{name} has {t.numel()} elements, plan needs {self.batch * self.n}")
+        if self.dtype == AMQFT_C64:
+            if t.dtype != torch.complex64 or not t.is_cuda or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous complex64 CUDA tensor")
+            if t.numel() != self.batch * self.n:
+                raise ValueError(f"{name} has {t.numel()} elements, plan needs {self.batch * self.n}")
+        else:
+            want = getattr(torch, _TORCH_16[self.dtype])
+            if t.dtype != want or not t.is_cuda or not t.is_contiguous() or t.shape[-1] != 2:
+                raise ValueError(f"{name} must be a contiguous {want} CUDA tensor of shape (..., N, 2)")
+            if t.numel() != 2 * self.batch * self.n:
+                raise ValueError(f"{name} has {t.numel() // 2} elements, plan needs {self.batch * self.n}")
 
-    def fwd(self, x, out=None, stream=None):
+    def _check_exp(self, e, name):
+        import torch
+
+        if e.dtype != torch.int32 or not e.is_cuda or not e.is_contiguous() or e.numel() != self.batch:
+            raise ValueError(f"{name} must be a contiguous int32 CUDA tensor of {self.batch} exponents")
+
+    def fwd(self, x, out=None, stream=None, exp_out=None):
         import torch
 
         self._check_tensor(x, "x")
         if out is None:
             out = torch.empty_like(x)
         self._check_tensor(out, "out")
-        amqft_exec_fwd(self.handle, x.data_ptr(), out.data_ptr(), 0, _stream_handle(stream))
-        return out
+        if self.dtype == AMQFT_C64:
+            amqft_exec_fwd(self.handle, x.data_ptr(), out.data_ptr(), 0, _stream_handle(stream))
+            return out
+        if exp_out is None:
+            exp_out = torch.empty(self.batch, dtype=torch.int32, device=x.device)
+        self._check_exp(exp_out, "exp_out")
+        amqft_exec_fwd(self.handle, x.data_ptr(), out.data_ptr(), exp_out.data_ptr(), _stream_handle(stream))
+        return out, exp_out
 
-    def inv(self, x, out=None, stream=None):
+    def inv(self, x, out=None, stream=None, exp_in=None, exp_out=None):
         import torch
 
         self._check_tensor(x, "x")
         if out is None:
             out = torch.empty_like(x)
         self._check_tensor(out, "out")
-        amqft_exec_inv(self.handle, x.data_ptr(), 0, out.data_ptr(), 0, _stream_handle(stream))
-        return out
+        if self.dtype == AMQFT_C64:
+            if exp_in is not None:
+                raise ValueError("exp_in is only used with 16-bit storage")
+            amqft_exec_inv(self.handle, x.data_ptr(), 0, out.data_ptr(), 0, _stream_handle(stream))
+            return out
+        if exp_in is not None:
+            self._check_exp(exp_in, "exp_in")
+        if exp_out is None:
+            exp_out = torch.empty(self.batch, dtype=torch.int32, device=x.device)
+        self._check_exp(exp_out, "exp_out")
+        amqft_exec_inv(self.handle, x.data_ptr(), exp_in.data_ptr() if exp_in is not None else 0, out.data_ptr(),
+                       exp_out.data_ptr(), _stream_handle(stream))
+        return out, exp_out
 
     def close(self):
         if getattr(self, "handle", 0):
@@ -165,6 +204,17 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+
+def dequantize(values, exps):
+    """complex128 tensor of values * 2^exp from 16-bit (batch, N, 2) storage
+    and its (batch,) int32 exponents (on the tensors' device)."""
+    import torch
+
+    v = values.to(torch.float64)
+    scale = torch.pow(torch.tensor(2.0, dtype=torch.float64, device=v.device), exps.to(torch.float64))
+    v = v * scale.reshape((-1,) + (1,) * (v.dim() - 1))
+    return torch.complex(v[..., 0], v[..., 1])
 
 
 def fft(x, variant: int = 4, inverse: bool = False):

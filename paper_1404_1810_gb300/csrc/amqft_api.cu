@@ -20,10 +20,7 @@ namespace amqft {
 FusedConfig fused_config(int logN) {
   FusedConfig c;
   const int N = 1 << logN, half = N >> 1;
-  const int padded = half + 2;
-  // regions of 64 or more values are padded to whole 32-float rows so the
-  // shared-memory swizzle stays inside the region
-  c.RS = logN >= 7 ? ((padded + 31) / 32) * 32 : ((padded + 1) / 2) * 2;
+  c.RS = region_stride(logN);
   if (logN <= 13) {
     c.cluster = 1;
     c.threads = 512;
@@ -70,6 +67,23 @@ static cudaError_t multipass_launch(int variant, const MpArgs& a, float* W0, flo
 __global__ void copy1_kernel(const float2* __restrict__ in, float2* __restrict__ out, long long batch) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < batch) out[i] = in[i];
+}
+
+// N = 1 with 16-bit storage: the value (conjugated for the inverse) gets the
+// exponent of its largest component, like every other length.
+__global__ void copy1_16_kernel(const unsigned* __restrict__ in, unsigned* __restrict__ out,
+                                const int* __restrict__ exp_in, int* __restrict__ exp_out, long long batch,
+                                int dtype) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < batch) {
+    const float s = exp_in ? pow2f(exp_in[i]) : 1.f;
+    const float2 v = unpack16(in[i], dtype);
+    const float re = v.x * s, im = v.y * s;
+    const int e = block_exponent(fmaxf(fabsf(re), fabsf(im)));
+    const float sc = pow2f(-e);
+    out[i] = pack16(re * sc, im * sc, dtype);
+    exp_out[i] = e;
+  }
 }
 
 }  // namespace amqft
@@ -178,7 +192,10 @@ extern "C" {
 
 const char* amqft_last_error(void) { return t_err.c_str(); }
 
-const char* amqft_version(void) { return "amqft 0.1 (sm_103a, fused single-pass, float32)"; }
+const char* amqft_version(void) {
+  return "amqft 0.2 (sm_103a; fused single-pass to 2^16, multi-pass to 2^24; float32 arithmetic; complex64, bf16 and "
+         "fp16 storage)";
+}
 
 int amqft_plan(amqft_plan_t* out, int log2n, int variant, int64_t batch, int dtype) {
   t_err.clear();
@@ -191,7 +208,8 @@ int amqft_plan(amqft_plan_t* out, int log2n, int variant, int64_t batch, int dty
     return fail(AMQFT_ERR_VARIANT,
                 "amqft_plan: variant %d (a recurrence variant) is limited to log2n <= %d; "
                 "variants 2, 4, 6, 8 reach %d", variant, AMQFT_LOG2N_FUSED_MAX, AMQFT_LOG2N_MAX);
-  if (dtype != AMQFT_C64) return fail(AMQFT_ERR_DTYPE, "amqft_plan: dtype=%d not supported (AMQFT_C64 only)", dtype);
+  if (dtype != AMQFT_C64 && dtype != AMQFT_CBF16 && dtype != AMQFT_CF16)
+    return fail(AMQFT_ERR_DTYPE, "amqft_plan: dtype=%d is not AMQFT_C64, AMQFT_CBF16 or AMQFT_CF16", dtype);
   if (batch < 0) return fail(AMQFT_ERR_ARG, "amqft_plan: batch=%lld < 0", (long long)batch);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -251,16 +269,23 @@ int amqft_plan(amqft_plan_t* out, int log2n, int variant, int64_t batch, int dty
   return AMQFT_OK;
 }
 
-static int exec(amqft_plan_t p, const void* in, void* out, int inverse, const void* e1, const void* e2,
+static int exec(amqft_plan_t p, const void* in, void* out, int inverse, const int32_t* exp_in, int32_t* exp_out,
                 void* stream) {
   t_err.clear();
   if (!p) return fail(AMQFT_ERR_ARG, "plan is NULL");
-  if (e1 || e2) return fail(AMQFT_ERR_DTYPE, "exponent arrays are only used with 16-bit storage");
+  const bool c64 = p->dtype == AMQFT_C64;
+  if (c64 && (exp_in || exp_out)) return fail(AMQFT_ERR_DTYPE, "exponent arrays are only used with 16-bit storage");
   if (p->batch == 0) return AMQFT_OK;
   if (!in || !out) return fail(AMQFT_ERR_ALIGN, "in or out is NULL");
-  if (((uintptr_t)in | (uintptr_t)out) & 7u) return fail(AMQFT_ERR_ALIGN, "in/out must be 8-byte aligned");
+  const uintptr_t amask = c64 ? 7u : 3u;
+  if (((uintptr_t)in | (uintptr_t)out) & amask)
+    return fail(AMQFT_ERR_ALIGN, "in/out must be %d-byte aligned", (int)amask + 1);
+  if (!c64) {
+    if (!exp_out) return fail(AMQFT_ERR_ARG, "16-bit storage needs exp_out (one int32 per transform)");
+    if (((uintptr_t)exp_out | (uintptr_t)exp_in) & 3u) return fail(AMQFT_ERR_ALIGN, "exponent arrays must be 4-byte aligned");
+  }
   const long long N = 1LL << p->log2n;
-  const uintptr_t bytes = (uintptr_t)(N * p->batch * 8);
+  const uintptr_t bytes = (uintptr_t)(N * p->batch * (c64 ? 8 : 4));
   const uintptr_t a0 = (uintptr_t)in, b0 = (uintptr_t)out;
   if (a0 < b0 + bytes && b0 < a0 + bytes) return fail(AMQFT_ERR_INPLACE, "in and out overlap");
   cudaStream_t st = (cudaStream_t)stream;
@@ -269,8 +294,11 @@ static int exec(amqft_plan_t p, const void* in, void* out, int inverse, const vo
     const long long per_buf = p->chunk * 4 * p->RSg;
     for (long long t0 = 0; t0 < p->batch; t0 += p->chunk) {
       MpArgs a;
-      a.in = (const float2*)in;
-      a.out = (float2*)out;
+      a.in = in;
+      a.out = out;
+      a.exp_in = exp_in;
+      a.exp_out = exp_out;
+      a.dtype = p->dtype;
       a.ctab = p->d_ctab;
       a.nt = (p->batch - t0) < p->chunk ? (p->batch - t0) : p->chunk;
       a.t0 = t0;
@@ -284,14 +312,19 @@ static int exec(amqft_plan_t p, const void* in, void* out, int inverse, const vo
   }
   if (p->log2n == 0) {
     const unsigned grid = (unsigned)((p->batch + 255) / 256);
-    copy1_kernel<<<grid, 256, 0, st>>>((const float2*)in, (float2*)out, p->batch);
+    if (c64) copy1_kernel<<<grid, 256, 0, st>>>((const float2*)in, (float2*)out, p->batch);
+    else copy1_16_kernel<<<grid, 256, 0, st>>>((const unsigned*)in, (unsigned*)out, exp_in, exp_out, p->batch,
+                                               p->dtype);
     e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_fail(e, "copy1_kernel launch");
+    if (e != cudaSuccess) return cuda_fail(e, "copy kernel launch");
     return AMQFT_OK;
   }
   FusedArgs a;
-  a.in = (const float2*)in;
-  a.out = (float2*)out;
+  a.in = in;
+  a.out = out;
+  a.exp_in = exp_in;
+  a.exp_out = exp_out;
+  a.dtype = p->dtype;
   a.ctab = p->d_ctab;
   a.batch = p->batch;
   a.logN = p->log2n;
@@ -305,7 +338,7 @@ static int exec(amqft_plan_t p, const void* in, void* out, int inverse, const vo
 }
 
 int amqft_exec_fwd(amqft_plan_t p, const void* in, void* out, int32_t* exp_out, void* stream) {
-  return exec(p, in, out, 0, exp_out, nullptr, stream);
+  return exec(p, in, out, 0, nullptr, exp_out, stream);
 }
 
 int amqft_exec_inv(amqft_plan_t p, const void* in, const int32_t* exp_in, void* out, int32_t* exp_out,

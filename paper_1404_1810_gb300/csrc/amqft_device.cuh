@@ -38,6 +38,8 @@
 #pragma once
 
 #include <cooperative_groups.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -57,8 +59,11 @@ struct SmallConsts {
 };
 
 struct FusedArgs {
-  const float2* in;
-  float2* out;
+  const void* in;      // complex64, or 16-bit complex pairs (dtype)
+  void* out;
+  const int* exp_in;   // 16-bit input: per-transform exponents (NULL: all 0)
+  int* exp_out;        // 16-bit output: per-transform exponents
+  int dtype;           // 0 complex64, 1 bf16 pairs, 2 fp16 pairs
   const float* ctab;   // device constant table, level-major, N/4 - 2 floats
   long long batch;
   int logN;
@@ -103,6 +108,13 @@ struct Div {
     return q;
   }
 };
+
+// Shared-memory stride of one region of a transform of 2^logN: N/2 + 2
+// values, padded to whole 32-float rows from N = 128 on (so the swizzle stays
+// inside the region).
+__host__ __device__ constexpr int region_stride(int logN) {
+  return logN >= 7 ? (((1 << (logN - 1)) + 2 + 31) / 32) * 32 : (((logN >= 1 ? (1 << (logN - 1)) : 0) + 3) / 2) * 2;
+}
 
 // Context (0 DCT, 1 DST) of the tree node of size 2^logLp at region position p0.
 template <int V>

@@ -34,14 +34,62 @@ struct Regions {
   }
 };
 
+// ---- HBM elements: complex64, or 16-bit complex (a bf16 or fp16 pair, real
+// part in the low half) holding value * 2^-exp with one exponent per
+// transform ----
+constexpr int DT_C64 = 0, DT_BF16 = 1, DT_F16 = 2;  // amqft_dtype
+
+struct InRef {
+  const void* p;
+  const int* exp;  // per-transform exponents of 16-bit input (NULL: all 0)
+  int dtype;
+};
+
+// 2^e as a float, exact (e clamped to the normal range)
+__device__ __forceinline__ float pow2f(int e) {
+  e = e < -126 ? -126 : (e > 127 ? 127 : e);
+  return __int_as_float((127 + e) << 23);
+}
+
+__device__ __forceinline__ float2 unpack16(unsigned u, int dtype) {
+  if (dtype == DT_BF16) return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+  return make_float2(__half2float(__ushort_as_half((unsigned short)(u & 0xffffu))),
+                     __half2float(__ushort_as_half((unsigned short)(u >> 16))));
+}
+
+__device__ __forceinline__ unsigned pack16(float re, float im, int dtype) {
+  if (dtype == DT_BF16)
+    return (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(re)) |
+           ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(im)) << 16);
+  return (unsigned)__half_as_ushort(__float2half_rn(re)) | ((unsigned)__half_as_ushort(__float2half_rn(im)) << 16);
+}
+
 __device__ __forceinline__ float2 ldz(const float2* __restrict__ p, int i, float cj) {
   float2 v = __ldcs(p + i);
   v.y *= cj;
   return v;
 }
 
+// 16-bit element times the transform's scale 2^exp (exact)
+__device__ __forceinline__ float2 ldz16(const unsigned* __restrict__ p, int i, int dtype, float s, float cj) {
+  float2 v = unpack16(__ldcs(p + i), dtype);
+  v.x *= s;
+  v.y *= s * cj;
+  return v;
+}
+
 __device__ __forceinline__ void stz(float2* __restrict__ p, int i, float re, float im, float cj) {
   __stcs(p + i, make_float2(re, im * cj));
+}
+
+// Exponent of a 16-bit output block whose largest component magnitude is m:
+// the stored values are below 2^14 in magnitude (fp16 reaches 65504).
+__device__ __forceinline__ int block_exponent(float m) {
+  if (!(m > 0.f) || !isfinite(m)) return 0;
+  int e = ((__float_as_int(m) >> 23) & 0xff) - 127;  // floor(log2 m) for normal m
+  if (e < -126) e = -126;
+  e -= 13;
+  return e < -100 ? -100 : (e > 100 ? 100 : e);
 }
 
 // Load stage for orbit item n of transform tau: samples n, N-n, N/2-n, N/2+n
@@ -51,22 +99,26 @@ struct Fetched {
   float2 a, b, c, d;
 };
 
-__device__ __forceinline__ Fetched load_fetch(const float2* __restrict__ in, int logN, long long t, int n, float cj) {
+__device__ __forceinline__ Fetched load_fetch(const InRef& in, int logN, long long t, int n, float cj) {
   const int N = 1 << logN, half = N >> 1, Q = N >> 2;
-  const float2* __restrict__ z = in + t * (long long)N;
+  const float2* __restrict__ z = static_cast<const float2*>(in.p) + t * (long long)N;
+  const unsigned* __restrict__ z16 = static_cast<const unsigned*>(in.p) + t * (long long)N;
+  const bool c64 = in.dtype == DT_C64;  // the same for every thread
+  const float s = (!c64 && in.exp) ? pow2f(__ldg(in.exp + t)) : 1.f;
+  auto ld = [&](int i) { return c64 ? ldz(z, i, cj) : ldz16(z16, i, in.dtype, s, cj); };
   Fetched f;
   if (n == 0) {
-    f.a = ldz(z, 0, cj);
-    f.b = ldz(z, half, cj);
+    f.a = ld(0);
+    f.b = ld(half);
     if (N >= 4) {
-      f.c = ldz(z, Q, cj);
-      f.d = ldz(z, 3 * Q, cj);
+      f.c = ld(Q);
+      f.d = ld(3 * Q);
     }
   } else {
-    f.a = ldz(z, n, cj);
-    f.b = ldz(z, N - n, cj);
-    f.c = ldz(z, half - n, cj);
-    f.d = ldz(z, half + n, cj);
+    f.a = ld(n);
+    f.b = ld(N - n);
+    f.c = ld(half - n);
+    f.d = ld(half + n);
   }
   return f;
 }
@@ -167,16 +219,24 @@ __device__ __forceinline__ Gathered store_gather(const RG& rg, int logN, int tau
   return g;
 }
 
+// The (up to) four outputs of orbit item k: harmonics k, N-k, N/2-k, N/2+k
+// (item 0: 0, N/2, N/4, 3N/4; N = 2: 0, 1).  Index -1 marks an unused slot.
+struct Out4 {
+  float2 v[4];
+  int i[4];
+};
+
 template <int V>
-__device__ __forceinline__ void store_emit(float2* __restrict__ out, int logN, long long t, int k, const Gathered& g,
-                                           float cj) {
+__device__ __forceinline__ Out4 emit_values(int logN, int k, const Gathered& g) {
   const int N = 1 << logN, half = N >> 1, Q = N >> 2;
-  float2* __restrict__ z = out + t * (long long)N;
+  Out4 o;
   if (k == 0) {
     if (N == 2) {
-      stz(z, 0, g.v[0], g.v[2], cj);
-      stz(z, 1, g.v[1], g.v[3], cj);
-      return;
+      o.v[0] = make_float2(g.v[0], g.v[2]); o.i[0] = 0;
+      o.v[1] = make_float2(g.v[1], g.v[3]); o.i[1] = 1;
+      o.i[2] = -1; o.i[3] = -1;
+      o.v[2] = o.v[3] = make_float2(0.f, 0.f);
+      return o;
     }
     float c01, c02, ch1, ch2;
     if constexpr (Var<V>::ot) {
@@ -186,11 +246,11 @@ __device__ __forceinline__ void store_emit(float2* __restrict__ out, int logN, l
       c01 = g.v[0]; ch1 = g.v[1]; c02 = g.v[2]; ch2 = g.v[3];
     }
     const float cq1 = g.v[4], cq2 = g.v[5], sq1 = g.v[6], sq2 = g.v[7];
-    stz(z, 0, c01, c02, cj);
-    stz(z, half, ch1, ch2, cj);
-    stz(z, Q, cq1 + sq2, cq2 - sq1, cj);
-    stz(z, 3 * Q, cq1 - sq2, cq2 + sq1, cj);
-    return;
+    o.v[0] = make_float2(c01, c02); o.i[0] = 0;
+    o.v[1] = make_float2(ch1, ch2); o.i[1] = half;
+    o.v[2] = make_float2(cq1 + sq2, cq2 - sq1); o.i[2] = Q;
+    o.v[3] = make_float2(cq1 - sq2, cq2 + sq1); o.i[3] = 3 * Q;
+    return o;
   }
   const int m = half - k;
   float ck1, ck2, cm1, cm2, sk1, sk2, sm1, sm2;
@@ -203,27 +263,234 @@ __device__ __forceinline__ void store_emit(float2* __restrict__ out, int logN, l
     sk1 = g.v[4]; sm1 = g.v[5]; sk2 = g.v[6]; sm2 = g.v[7];
   }
   // D_c^F with Re R = DCT, Im R = -DST: X(k) = (C1 + S2, C2 - S1), X(N-k) = (C1 - S2, C2 + S1)
-  stz(z, k, ck1 + sk2, ck2 - sk1, cj);
-  stz(z, N - k, ck1 - sk2, ck2 + sk1, cj);
-  stz(z, m, cm1 + sm2, cm2 - sm1, cj);
-  stz(z, half + k, cm1 - sm2, cm2 + sm1, cj);
+  o.v[0] = make_float2(ck1 + sk2, ck2 - sk1); o.i[0] = k;
+  o.v[1] = make_float2(ck1 - sk2, ck2 + sk1); o.i[1] = N - k;
+  o.v[2] = make_float2(cm1 + sm2, cm2 - sm1); o.i[2] = m;
+  o.v[3] = make_float2(cm1 - sm2, cm2 + sm1); o.i[3] = half + k;
+  return o;
 }
 
-template <int V, int TPB, int MAXI, int CL>
+__device__ __forceinline__ float out4_absmax(const Out4& o) {
+  float m = 0.f;
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (o.i[j] >= 0) m = fmaxf(m, fmaxf(fabsf(o.v[j].x), fabsf(o.v[j].y)));
+  return m;
+}
+
+template <int V>
+__device__ __forceinline__ void store_emit(float2* __restrict__ out, int logN, long long t, int k, const Gathered& g,
+                                           float cj) {
+  const Out4 o = emit_values<V>(logN, k, g);
+  float2* __restrict__ z = out + t * (long long)(1 << logN);
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (o.i[j] >= 0) stz(z, o.i[j], o.v[j].x, o.v[j].y, cj);
+}
+
+// 16-bit output of one item, every value times s = 2^-exp (exact)
+__device__ __forceinline__ void store16(unsigned* __restrict__ out, int logN, long long t, const Out4& o, float s,
+                                        float cj, int dtype) {
+  unsigned* __restrict__ z = out + t * (long long)(1 << logN);
+#pragma unroll
+  for (int j = 0; j < 4; ++j)
+    if (o.i[j] >= 0) __stcs(z + o.i[j], pack16(o.v[j].x * s, o.v[j].y * (s * cj), dtype));
+}
+
+// ---------------------------------------------------------------------
+// store of the cluster path, in two stages
+// ---------------------------------------------------------------------
+// Stage 1, local: the CTA's own region is rewritten in natural frequency
+// order, unswizzled (word k holds DCT/DST value k; DST words 0 and N/2 hold
+// 0).  Time-first variants apply the last chain level here (D_n frequency
+// phase, M = N): dct S(k) = E(k) + O(k), S(N/2-k) = E(k) - O(k), with E the
+// dct(N/2) result at [Q, 2Q] and O the dct_ot(N) result in bit-reversed order
+// at [0, Q); dst S(k) = O(k-1) + E(k-1), S(N/2-k) = O(k-1) - E(k-1),
+// S(Q) = O(Q-1).  Harmonics-first variants only undo the chain layout.
+// Every thread reads its values, then the block synchronises, then writes.
+template <int V, int TPB, int LN>
+__device__ __forceinline__ void region_to_natural(float* R, int ctx) {
+  constexpr int N = 1 << LN, half = N >> 1, Q = N >> 2, logQ = LN - 2;
+  if constexpr (Var<V>::ot) {
+    constexpr int NI = Q / TPB;
+    float a[NI], b[NI];
+    float mid = 0.f;
+#pragma unroll
+    for (int s = 0; s < NI; ++s) {
+      const int j = threadIdx.x + s * TPB;
+      const float o = R[sw(brev(j, logQ))];
+      if (ctx == 0) {
+        const float e = R[sw(Q + j)];
+        a[s] = e + o;
+        b[s] = e - o;
+      } else if (j < Q - 1) {
+        const float e = R[sw(Q + j)];
+        a[s] = o + e;
+        b[s] = o - e;
+      } else {
+        a[s] = o;  // S(Q)
+        b[s] = 0.f;
+      }
+    }
+    if (ctx == 0 && threadIdx.x == 0) mid = R[sw(half)];  // C(Q) = E(Q)
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < NI; ++s) {
+      const int j = threadIdx.x + s * TPB;
+      if (ctx == 0) {
+        R[j] = a[s];
+        R[half - j] = b[s];
+      } else if (j < Q - 1) {
+        R[j + 1] = a[s];
+        R[half - j - 1] = b[s];
+      } else {
+        R[Q] = a[s];
+      }
+    }
+    if (threadIdx.x == 0) {
+      if (ctx == 0) {
+        R[Q] = mid;
+      } else {
+        R[0] = 0.f;
+        R[half] = 0.f;
+      }
+    }
+  } else {
+    constexpr int NI = half / TPB;
+    float a[NI];
+    float last = 0.f;
+#pragma unroll
+    for (int s = 0; s < NI; ++s) {
+      const int k = threadIdx.x + s * TPB;
+      a[s] = (ctx == 0 || k > 0) ? R[sw(pos_chain(k, LN, ctx))] : 0.f;
+    }
+    if (ctx == 0 && threadIdx.x == 0) last = R[sw(half)];  // C(N/2)
+    __syncthreads();
+#pragma unroll
+    for (int s = 0; s < NI; ++s) R[threadIdx.x + s * TPB] = a[s];
+    if (threadIdx.x == 0) R[half] = last;
+  }
+}
+
+// Stage 2, across the cluster: D_r^F (Eq. qft_24-25: Re R = DCT, Im R = -DST)
+// and D_c^F (Eq. qft_17-21) for four consecutive harmonics per step, the four
+// regions read as float4 through distributed shared memory:
+//   X(k) = (C1 + S2, C2 - S1),  X(N-k) = (C1 - S2, C2 + S1),  k = 1..N/2-1,
+//   X(0) = (C1(0), C2(0)),  X(N/2) = (C1(N/2), C2(N/2)).
+// CTA r of the cluster (region r) covers k in [r N/8, (r+1) N/8).
+template <int TPB, int LN>
+__device__ __forceinline__ void store_natural_cluster(float* sm, const FusedArgs& a, long long t, float cj,
+                                                      float* red) {
+  constexpr int N = 1 << LN, half = N >> 1, PER = half / 4, NG = PER / 4 / TPB;
+  static_assert(NG * 4 * TPB == PER, "four harmonics per thread and step");
+  cg::cluster_group cl = cg::this_cluster();
+  const int rank = (int)cl.block_rank();
+  const float4* C1 = reinterpret_cast<const float4*>(cl.map_shared_rank(sm, 0));
+  const float4* S1 = reinterpret_cast<const float4*>(cl.map_shared_rank(sm, 1));
+  const float4* C2 = reinterpret_cast<const float4*>(cl.map_shared_rank(sm, 2));
+  const float4* S2 = reinterpret_cast<const float4*>(cl.map_shared_rank(sm, 3));
+  // X(k0 + i) -> f[i], X(N - k0 - i) -> b[i] (k0 = 0: b[0] = X(N/2))
+  auto group = [&](int gi, float2 (&f)[4], float2 (&b)[4]) {
+    const int k0 = rank * PER + 4 * ((int)threadIdx.x + gi * TPB);
+    const float4 c1 = C1[k0 >> 2], s1 = S1[k0 >> 2], c2 = C2[k0 >> 2], s2 = S2[k0 >> 2];
+    const float a1[4] = {c1.x, c1.y, c1.z, c1.w}, b1[4] = {s1.x, s1.y, s1.z, s1.w};
+    const float a2[4] = {c2.x, c2.y, c2.z, c2.w}, b2[4] = {s2.x, s2.y, s2.z, s2.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      f[i] = make_float2(a1[i] + b2[i], a2[i] - b1[i]);
+      b[i] = make_float2(a1[i] - b2[i], a2[i] + b1[i]);
+    }
+    if (k0 == 0) {  // X(0) = (C1(0), C2(0)); X(N/2) = (C1(N/2), C2(N/2))
+      f[0] = make_float2(a1[0], a2[0]);
+      b[0] = make_float2(cl.map_shared_rank(sm, 0)[half], cl.map_shared_rank(sm, 2)[half]);
+    }
+    return k0;
+  };
+  if (a.dtype == DT_C64) {
+    float2* __restrict__ z = static_cast<float2*>(a.out) + t * (long long)N;
+    const bool vec_ok = (reinterpret_cast<uintptr_t>(a.out) & 15u) == 0;  // same for every thread
+#pragma unroll
+    for (int gi = 0; gi < NG; ++gi) {
+      float2 f[4], b[4];
+      const int k0 = group(gi, f, b);
+      if (vec_ok) {
+        __stcs(reinterpret_cast<float4*>(z + k0), make_float4(f[0].x, f[0].y * cj, f[1].x, f[1].y * cj));
+        __stcs(reinterpret_cast<float4*>(z + k0 + 2), make_float4(f[2].x, f[2].y * cj, f[3].x, f[3].y * cj));
+      } else {  // out is only 8-byte aligned
+#pragma unroll
+        for (int i = 0; i < 4; ++i) stz(z, k0 + i, f[i].x, f[i].y, cj);
+      }
+#pragma unroll
+      for (int i = 0; i < 4; ++i) stz(z, k0 == 0 && i == 0 ? half : N - k0 - i, b[i].x, b[i].y, cj);
+    }
+    return;
+  }
+  // 16-bit: the largest component magnitude of the transform fixes its
+  // exponent; the outputs are then recomputed, scaled by 2^-exp and rounded
+  float m = 0.f;
+#pragma unroll
+  for (int gi = 0; gi < NG; ++gi) {
+    float2 f[4], b[4];
+    group(gi, f, b);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      m = fmaxf(m, fmaxf(fmaxf(fabsf(f[i].x), fabsf(f[i].y)), fmaxf(fabsf(b[i].x), fabsf(b[i].y))));
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, d));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float bm = 0.f;
+    for (int w = 0; w < TPB / 32; ++w) bm = fmaxf(bm, red[w]);
+    sm[half + 1] = bm;  // word N/2 + 1 of the region is free
+  }
+  cl.sync();
+  float M = 0.f;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) M = fmaxf(M, cl.map_shared_rank(sm, r)[half + 1]);
+  const int e = block_exponent(M);
+  const float sc = pow2f(-e), si = sc * cj;
+  if (rank == 0 && threadIdx.x == 0) a.exp_out[t] = e;
+  unsigned* __restrict__ z = static_cast<unsigned*>(a.out) + t * (long long)N;
+  const bool vec_ok = (reinterpret_cast<uintptr_t>(a.out) & 15u) == 0;
+#pragma unroll
+  for (int gi = 0; gi < NG; ++gi) {
+    float2 f[4], b[4];
+    const int k0 = group(gi, f, b);
+    unsigned u[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) u[i] = pack16(f[i].x * sc, f[i].y * si, a.dtype);
+    if (vec_ok) {
+      __stcs(reinterpret_cast<uint4*>(z + k0), make_uint4(u[0], u[1], u[2], u[3]));
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) __stcs(z + k0 + i, u[i]);
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      __stcs(z + (k0 == 0 && i == 0 ? half : N - k0 - i), pack16(b[i].x * sc, b[i].y * si, a.dtype));
+  }
+}
+
+// LN > 0: the kernel is compiled for log2 N = LN (every index computation
+// is then resolved at compile time); LN == 0: a.logN at run time.
+template <int V, int TPB, int MAXI, int CL, int LN>
 __global__ void __launch_bounds__(TPB) fused_kernel(const FusedArgs a, const __grid_constant__ SmallConsts K) {
   extern __shared__ __align__(16) float sm[];
-  const int logN = a.logN, N = 1 << logN, half = N >> 1;
+  const int logN = LN > 0 ? LN : a.logN, N = 1 << logN, half = N >> 1;
+  const int RS = LN > 0 ? region_stride(LN) : a.RS;
   const int Qi = N >= 4 ? (N >> 2) : 1;   // orbit items per transform
   const int logQi = N >= 4 ? logN - 2 : 0;
   const float cj = a.inverse ? -1.f : 1.f;
   Geo g;
   g.logN = logN;
   g.half = half;
-  g.RS = a.RS;
+  g.RS = RS;
   g.sub = 0;
   Regions<CL> rg;
   rg.sm = sm;
-  rg.RS = a.RS;
+  rg.RS = RS;
   int ntr;
   if constexpr (CL == 1) {
     rg.tbase = (long long)blockIdx.x * a.tpc;
@@ -244,13 +511,14 @@ __global__ void __launch_bounds__(TPB) fused_kernel(const FusedArgs a, const __g
   float* snap = wsum + 32;
 
   // ---- load ----
-  // every configuration gives each thread exactly four orbit items
+  // every configuration gives each thread exactly NIT orbit items
+  constexpr int NIT = (CL > 1 && LN > 0) ? (1 << (LN - 4)) / TPB : 4;
   {
-    int n_[4], tau_[4];
-    bool ok_[4];
-    Fetched f_[4];
+    int n_[NIT], tau_[NIT];
+    bool ok_[NIT];
+    Fetched f_[NIT];
 #pragma unroll
-    for (int s = 0; s < 4; ++s) {
+    for (int s = 0; s < NIT; ++s) {
       if constexpr (CL == 1) {
         const int w = threadIdx.x + s * TPB;
         tau_[s] = w >> logQi;
@@ -262,11 +530,11 @@ __global__ void __launch_bounds__(TPB) fused_kernel(const FusedArgs a, const __g
         n_[s] = (int)cg::this_cluster().block_rank() * per + threadIdx.x + s * TPB;
         ok_[s] = (int)threadIdx.x + s * TPB < per;
       }
-      if (ok_[s]) f_[s] = load_fetch(a.in, a.logN, rg.tbase + tau_[s], n_[s], cj);
+      if (ok_[s]) f_[s] = load_fetch(InRef{a.in, a.exp_in, a.dtype}, logN, rg.tbase + tau_[s], n_[s], cj);
     }
 #pragma unroll
-    for (int s = 0; s < 4; ++s)
-      if (ok_[s]) load_scatter<V>(rg, a.logN, tau_[s], n_[s], f_[s]);
+    for (int s = 0; s < NIT; ++s)
+      if (ok_[s]) load_scatter<V>(rg, logN, tau_[s], n_[s], f_[s]);
   }
   if constexpr (CL == 1) __syncthreads();
   else cg::this_cluster().sync();
@@ -275,6 +543,7 @@ __global__ void __launch_bounds__(TPB) fused_kernel(const FusedArgs a, const __g
   const int logTop = logN - 2;  // log2 of the largest tree (N/4)
   const BandPlan bp = band_plan(logN);
   if constexpr (Var<V>::ot) {
+#pragma unroll
     for (int b = 0; b < bp.nb; ++b) {
       run_fold_band_r<V, TPB>(sm, g, bp.logL[b], bp.R[b], true, a.ctab);
       __syncthreads();
@@ -301,6 +570,7 @@ __global__ void __launch_bounds__(TPB) fused_kernel(const FusedArgs a, const __g
         __syncthreads();
       }
     } else {
+#pragma unroll
       for (int b = bp.nb - 1; b >= 0; --b) {
         run_chunk_band_r<V, TPB>(sm, snap, g, bp.logL[b], bp.R[b]);
         __syncthreads();
@@ -333,6 +603,7 @@ __global__ void __launch_bounds__(TPB) fused_kernel(const FusedArgs a, const __g
       }
       __syncthreads();
     }
+#pragma unroll
     for (int b = bp.nb - 1; b >= 0; --b) {
       run_fold_band_r<V, TPB>(sm, g, bp.logL[b], bp.R[b], false, a.ctab);
       __syncthreads();
@@ -340,6 +611,14 @@ __global__ void __launch_bounds__(TPB) fused_kernel(const FusedArgs a, const __g
   }
 
   // ---- store ----
+  if constexpr (CL > 1 && LN > 0) {
+    __syncthreads();
+    region_to_natural<V, TPB, LN>(sm, (int)cg::this_cluster().block_rank() & 1);
+    cg::this_cluster().sync();
+    store_natural_cluster<TPB, LN>(sm, a, rg.tbase, cj, tot);
+    cg::this_cluster().sync();  // keep shared memory alive for the other CTAs' reads
+    return;
+  }
   if constexpr (CL > 1) cg::this_cluster().sync();
   {
     int k_[4], tau_[4];
@@ -358,11 +637,36 @@ __global__ void __launch_bounds__(TPB) fused_kernel(const FusedArgs a, const __g
         k_[s] = (int)cg::this_cluster().block_rank() * per + threadIdx.x + s * TPB;
         ok_[s] = (int)threadIdx.x + s * TPB < per;
       }
-      if (ok_[s]) g_[s] = store_gather<V>(rg, a.logN, tau_[s], k_[s]);
+      if (ok_[s]) g_[s] = store_gather<V>(rg, logN, tau_[s], k_[s]);
     }
+    if (a.dtype == DT_C64) {
 #pragma unroll
-    for (int s = 0; s < 4; ++s)
-      if (ok_[s]) store_emit<V>(a.out, a.logN, rg.tbase + tau_[s], k_[s], g_[s], cj);
+      for (int s = 0; s < 4; ++s)
+        if (ok_[s]) store_emit<V>(static_cast<float2*>(a.out), logN, rg.tbase + tau_[s], k_[s], g_[s], cj);
+    } else {
+      // 16-bit: one exponent per transform from its largest component
+      static_assert(CL == 1 || LN > 0, "the cluster path stores through store_natural_cluster");
+      Out4 o_[4];
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+        if (ok_[s]) o_[s] = emit_values<V>(logN, k_[s], g_[s]);
+      __syncthreads();  // every gather is done: region memory is free
+      int* slot = reinterpret_cast<int*>(sm);
+      for (int i = threadIdx.x; i < ntr; i += TPB) slot[i] = 0;
+      __syncthreads();
+#pragma unroll
+      for (int s = 0; s < 4; ++s)
+        if (ok_[s]) atomicMax(slot + tau_[s], __float_as_int(out4_absmax(o_[s])));
+      __syncthreads();
+#pragma unroll
+      for (int s = 0; s < 4; ++s) {
+        if (ok_[s]) {
+          const int e = block_exponent(__int_as_float(slot[tau_[s]]));
+          store16(static_cast<unsigned*>(a.out), logN, rg.tbase + tau_[s], o_[s], pow2f(-e), cj, a.dtype);
+          if (k_[s] == 0) a.exp_out[rg.tbase + tau_[s]] = e;
+        }
+      }
+    }
   }
   if constexpr (CL > 1) cg::this_cluster().sync();  // keep shared memory alive for the other CTAs' reads
 }
@@ -370,10 +674,10 @@ __global__ void __launch_bounds__(TPB) fused_kernel(const FusedArgs a, const __g
 // ---------------------------------------------------------------------
 // host side: configuration and launch
 // ---------------------------------------------------------------------
-template <int V, int TPB, int MAXI, int CL>
+template <int V, int TPB, int MAXI, int CL, int LN>
 cudaError_t launch_cfg(const FusedArgs& a, const SmallConsts& K, long long grid, int smem,
                               cudaStream_t st) {
-  auto kern = fused_kernel<V, TPB, MAXI, CL>;
+  auto kern = fused_kernel<V, TPB, MAXI, CL, LN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   if constexpr (CL == 1) {
@@ -400,12 +704,12 @@ template <int V>
 cudaError_t launch_v(const FusedArgs& a, const SmallConsts& K, const FusedConfig& c, cudaStream_t st) {
   if (c.cluster == 1) {
     const long long grid = (a.batch + c.per_cta - 1) / c.per_cta;
-    return launch_cfg<V, 512, 16, 1>(a, K, grid, c.smem, st);
+    return launch_cfg<V, 512, 16, 1, 0>(a, K, grid, c.smem, st);
   }
-  switch (c.threads) {
-    case 256: return launch_cfg<V, 256, 16, 4>(a, K, a.batch, c.smem, st);
-    case 512: return launch_cfg<V, 512, 16, 4>(a, K, a.batch, c.smem, st);
-    default: return launch_cfg<V, 1024, 16, 4>(a, K, a.batch, c.smem, st);
+  switch (a.logN) {
+    case 14: return launch_cfg<V, 256, 16, 4, 14>(a, K, a.batch, c.smem, st);
+    case 15: return launch_cfg<V, 512, 16, 4, 15>(a, K, a.batch, c.smem, st);
+    default: return launch_cfg<V, 1024, 16, 4, 16>(a, K, a.batch, c.smem, st);
   }
 }
 

@@ -28,8 +28,11 @@ constexpr int MP_S = 1 << MP_LOG_S;
 constexpr int MP_TPB = 512;            // solve CTA: 16384 values, 32 per thread
 
 struct MpArgs {
-  const float2* in;
-  float2* out;
+  const void* in;      // complex64, or 16-bit complex pairs (dtype)
+  void* out;
+  const int* exp_in;   // 16-bit input: per-transform exponents (NULL: all 0)
+  int* exp_out;        // 16-bit output: per-transform exponents
+  int dtype;
   const float* ctab;
   long long nt;       // transforms in this chunk
   long long t0;       // first transform of the chunk (for in/out)
@@ -53,7 +56,7 @@ __global__ void mp_load_kernel(MpArgs a, float* W) {
   for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
     const long long t = w >> logQ;
     const int n = (int)(w & ((1LL << logQ) - 1));
-    const Fetched f = load_fetch(a.in, a.logN, a.t0 + t, n, cj);
+    const Fetched f = load_fetch(InRef{a.in, a.exp_in, a.dtype}, a.logN, a.t0 + t, n, cj);
     load_scatter<V>(rg, a.logN, (int)t, n, f);
   }
 }
@@ -68,7 +71,46 @@ __global__ void mp_store_kernel(MpArgs a, const float* W) {
     const long long t = w >> logQ;
     const int k = (int)(w & ((1LL << logQ) - 1));
     const Gathered g = store_gather<V>(rg, a.logN, (int)t, k);
-    store_emit<V>(a.out, a.logN, a.t0 + t, k, g, cj);
+    store_emit<V>(static_cast<float2*>(a.out), a.logN, a.t0 + t, k, g, cj);
+  }
+}
+
+// 16-bit output, pass 1: the largest component magnitude of each transform
+// of the chunk, as float bits in Mx[t] (zeroed by mp_zero_kernel)
+template <int V>
+__global__ void mp_max_kernel(MpArgs a, const float* W, int* Mx) {
+  const int logQ = a.logN - 2;
+  const long long total = a.nt << logQ;
+  GRegions rg{const_cast<float*>(W), a.RSg};
+  for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
+    const long long t = w >> logQ;
+    const int k = (int)(w & ((1LL << logQ) - 1));
+    const Out4 o = emit_values<V>(a.logN, k, store_gather<V>(rg, a.logN, (int)t, k));
+    const float m = out4_absmax(o);
+    if (m > 0.f) atomicMax(Mx + t, __float_as_int(m));
+  }
+}
+
+template <int V>
+__global__ void mp_zero_kernel(int* Mx, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) Mx[i] = 0;
+}
+
+// 16-bit output, pass 2: exponent per transform, outputs scaled by 2^-exp
+template <int V>
+__global__ void mp_store16_kernel(MpArgs a, const float* W, const int* Mx) {
+  const int logQ = a.logN - 2;
+  const long long total = a.nt << logQ;
+  const float cj = a.inverse ? -1.f : 1.f;
+  GRegions rg{const_cast<float*>(W), a.RSg};
+  for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
+    const long long t = w >> logQ;
+    const int k = (int)(w & ((1LL << logQ) - 1));
+    const Out4 o = emit_values<V>(a.logN, k, store_gather<V>(rg, a.logN, (int)t, k));
+    const int e = block_exponent(__int_as_float(Mx[t]));
+    store16(static_cast<unsigned*>(a.out), a.logN, a.t0 + t, o, pow2f(-e), cj, a.dtype);
+    if (k == 0) a.exp_out[a.t0 + t] = e;
   }
 }
 
@@ -371,7 +413,17 @@ cudaError_t mp_run(const MpArgs& a0, float* W0, float* W1, const SmallConsts& K,
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
   }
-  mp_store_kernel<V><<<grid_for(a.nt * (N / 4)), threads, 0, st>>>(a, cur);
+  if (a.dtype == 0) {
+    mp_store_kernel<V><<<grid_for(a.nt * (N / 4)), threads, 0, st>>>(a, cur);
+    return cudaGetLastError();
+  }
+  // 16-bit: the free ping-pong buffer holds the per-transform maxima
+  int* Mx = reinterpret_cast<int*>(oth);
+  mp_zero_kernel<V><<<(unsigned)((a.nt + 255) / 256), 256, 0, st>>>(Mx, a.nt);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  mp_max_kernel<V><<<grid_for(a.nt * (N / 4)), threads, 0, st>>>(a, cur, Mx);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  mp_store16_kernel<V><<<grid_for(a.nt * (N / 4)), threads, 0, st>>>(a, cur, Mx);
   return cudaGetLastError();
 }
 

@@ -113,8 +113,11 @@ extern "C" int amqft_exec_static(amqft_plan_t plan, int64_t batch, const void* i
   cudaStream_t st = (cudaStream_t)stream;
   for (long long t0 = 0; t0 < batch; t0 += chunk) {
     MpArgs a;
-    a.in = (const float2*)in;
-    a.out = (float2*)out;
+    a.in = in;
+    a.out = out;
+    a.exp_in = nullptr;
+    a.exp_out = nullptr;
+    a.dtype = AMQFT_C64;
     a.ctab = pv.ctab;
     a.nt = (batch - t0) < chunk ? (batch - t0) : chunk;
     a.t0 = t0;

@@ -189,3 +189,30 @@ def test_tiny_lengths(orc, log2n):
         for b in range(5):
             r32 = orc.amqft(x[b].astype(np.complex64).astype(np.complex128), v, prec="f32")
             assert np.array_equal(y[b].astype(np.complex64), r32.astype(np.complex64))
+
+
+@pytest.mark.parametrize("v", [4, 2, 1])
+@pytest.mark.parametrize("log2n", [14, 16])
+def test_output_only_8_byte_aligned(v, log2n):
+    """out may be 8-byte but not 16-byte aligned: same results as an aligned out."""
+    import torch
+
+    from paper_1404_1810_gb300 import Plan, amqft_exec_fwd, amqft_exec_inv
+
+    n, b = 1 << log2n, 3
+    x = synth.device_normal_complex64(n, b, "cuda", seed_offset=77)
+    p = Plan(log2n, v, b)
+    try:
+        ref_f = p.fwd(x)
+        ref_i = p.inv(x)
+        buf = torch.zeros(b * n + 1, dtype=torch.complex64, device="cuda")
+        ptr = buf.data_ptr() + 8
+        assert ptr % 16 == 8
+        amqft_exec_fwd(p.handle, x.data_ptr(), ptr, 0, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert torch.equal(buf[1:].reshape(b, n), ref_f)
+        amqft_exec_inv(p.handle, x.data_ptr(), 0, ptr, 0, torch.cuda.current_stream().cuda_stream)
+        torch.cuda.synchronize()
+        assert torch.equal(buf[1:].reshape(b, n), ref_i)
+    finally:
+        p.close()

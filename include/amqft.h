@@ -106,6 +106,51 @@ const char *amqft_version(void);
 int amqft_plan_info(amqft_plan_t plan, int *cluster, int *per_cta, int *threads, int *smem_bytes);
 
 /* ---------------------------------------------------------------------
+ * Ragged batches: many transforms of different power-of-two lengths, each at
+ * its own offset, in one call that launches a fixed sequence of kernels and
+ * makes no host synchronisation (capturable in a CUDA graph once the plan
+ * exists; the first call also sets kernel attributes, so make one eager call
+ * before capturing).
+ */
+
+/* Plan for ragged batches of up to max_count transforms, each of length
+ * 2^k with 0 <= k <= max_log2n, and at most max_points points of lengths above
+ * 2^AMQFT_LOG2N_FUSED_MAX in one batch.  Owns the constant table of the longest
+ * length (it holds those of every shorter length), the per-length id lists
+ * ((max_log2n + 1) * max_count int32) and, when max_log2n > 16, a multi-pass
+ * workspace of about 16 bytes per point of max_points.  AMQFT_C64 only.
+ * Errors: as amqft_plan, plus AMQFT_ERR_ARG (max_count outside [1, 2^30],
+ * max_points < 1), AMQFT_ERR_DTYPE (16-bit storage), AMQFT_ERR_NOMEM. */
+int amqft_plan_ragged(amqft_plan_t *out, int max_log2n, int variant, int dtype, int64_t max_count,
+                      int64_t max_points);
+
+/* Transform `count` (<= max_count) ragged transforms: transform i has
+ * 2^d_log2n[i] interleaved complex64 elements starting at element
+ * d_offsets[i] of in (read) and of out (written); forward (direction 0) or
+ * unnormalised inverse (direction 1).  d_offsets (int64) and d_log2n (uint8)
+ * are device arrays of `count` entries; in, out and d_offsets are 8-byte
+ * aligned; the transforms must not overlap each other or between in and out.
+ * Transforms whose log2 N exceeds the plan's, and multi-pass transforms beyond
+ * the max_points capacity, are skipped and counted (amqft_ragged_skipped).
+ * Each transform gives exactly the result of amqft_exec_fwd/inv of a plan of
+ * its length.  Errors: AMQFT_ERR_ARG (not a ragged plan, count outside
+ * [0, max_count], direction not 0/1), AMQFT_ERR_ALIGN, AMQFT_ERR_CUDA. */
+int amqft_exec_ragged(amqft_plan_t plan, int64_t count, const int64_t *d_offsets, const uint8_t *d_log2n,
+                      const void *in, void *out, int direction, void *stream);
+
+/* Launch knobs of a ragged plan, set by the autotuner: knob 0 schedule of
+ * the persistent small-length launch (0 static, 1 dynamic work counter;
+ * default 1), knob 1 order of its work items (0 longest lengths first, 1
+ * shortest first; default 0), knob 2 its CTAs per SM (1..4; default 1),
+ * knob 3 cluster grid multiplier of the 2^14..2^16 launches (1..4; default 1).
+ * Errors: AMQFT_ERR_ARG. */
+int amqft_ragged_tune(amqft_plan_t plan, int knob, int value);
+
+/* Number of transforms the last amqft_exec_ragged call skipped.  Waits for
+ * the device (cudaMemcpy).  Errors: AMQFT_ERR_ARG, AMQFT_ERR_CUDA. */
+int amqft_ragged_skipped(amqft_plan_t plan, int64_t *skipped);
+
+/* ---------------------------------------------------------------------
  * Allocation-free execution.  The paper has no counterpart to this entry
  * point: it runs the same multi-pass kernels as amqft_exec_fwd/inv, with
  * their workspace in a fixed device array compiled into the library instead

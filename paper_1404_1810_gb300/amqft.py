@@ -51,6 +51,14 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.amqft_destroy.restype = i32
         lib.amqft_last_error.restype = ctypes.c_char_p
         lib.amqft_version.restype = ctypes.c_char_p
+        lib.amqft_plan_ragged.argtypes = [ctypes.POINTER(vp), i32, i32, i32, i64, i64]
+        lib.amqft_plan_ragged.restype = i32
+        lib.amqft_exec_ragged.argtypes = [vp, i64, vp, vp, vp, vp, i32, vp]
+        lib.amqft_exec_ragged.restype = i32
+        lib.amqft_ragged_tune.argtypes = [vp, i32, i32]
+        lib.amqft_ragged_tune.restype = i32
+        lib.amqft_ragged_skipped.argtypes = [vp, ctypes.POINTER(i64)]
+        lib.amqft_ragged_skipped.restype = i32
         lib.amqft_exec_static.argtypes = [vp, i64, vp, vp, i32, vp]
         lib.amqft_exec_static.restype = i32
         lib.amqft_plan_info.argtypes = [vp] + [ctypes.POINTER(i32)] * 4
@@ -86,6 +94,29 @@ def amqft_exec_static(plan: int, batch: int, d_in: int, d_out: int, inverse: int
     no allocation in the call; calls overlapping in time on one device race."""
     _check(load().amqft_exec_static(plan, int(batch), d_in, d_out, int(inverse), stream or None),
            "amqft_exec_static")
+
+
+def amqft_plan_ragged(max_log2n: int, variant: int, dtype: int, max_count: int, max_points: int) -> int:
+    h = ctypes.c_void_p()
+    _check(load().amqft_plan_ragged(ctypes.byref(h), int(max_log2n), int(variant), int(dtype), int(max_count),
+                                    int(max_points)), "amqft_plan_ragged")
+    return int(h.value)
+
+
+def amqft_exec_ragged(plan: int, count: int, d_offsets: int, d_log2n: int, d_in: int, d_out: int,
+                      direction: int = 0, stream: int = 0) -> None:
+    _check(load().amqft_exec_ragged(plan, int(count), d_offsets, d_log2n, d_in, d_out, int(direction),
+                                    stream or None), "amqft_exec_ragged")
+
+
+def amqft_ragged_tune(plan: int, knob: int, value: int) -> None:
+    _check(load().amqft_ragged_tune(plan, int(knob), int(value)), "amqft_ragged_tune")
+
+
+def amqft_ragged_skipped(plan: int) -> int:
+    v = ctypes.c_int64()
+    _check(load().amqft_ragged_skipped(plan, ctypes.byref(v)), "amqft_ragged_skipped")
+    return int(v.value)
 
 
 def amqft_destroy(plan: int) -> None:
@@ -193,6 +224,53 @@ class Plan:
         amqft_exec_inv(self.handle, x.data_ptr(), exp_in.data_ptr() if exp_in is not None else 0, out.data_ptr(),
                        exp_out.data_ptr(), _stream_handle(stream))
         return out, exp_out
+
+    def close(self):
+        if getattr(self, "handle", 0):
+            amqft_destroy(self.handle)
+            self.handle = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class RaggedPlan:
+    """Owns a ragged plan: exec() transforms, in one call, `count` complex64
+    transforms of lengths 2^log2n[i] at element offsets offsets[i] of flat
+    complex64 CUDA tensors (log2n: uint8, offsets: int64, both on the device)."""
+
+    KNOBS = ("schedule", "order", "small_ctas_per_sm", "cluster_mult")
+
+    def __init__(self, max_log2n: int, variant: int, max_count: int, max_points: int):
+        self.max_log2n, self.variant = int(max_log2n), int(variant)
+        self.max_count, self.max_points = int(max_count), int(max_points)
+        self.handle = amqft_plan_ragged(self.max_log2n, self.variant, AMQFT_C64, self.max_count, self.max_points)
+        self.knobs = {"schedule": 1, "order": 0, "small_ctas_per_sm": 1, "cluster_mult": 1}
+
+    def tune(self, **knobs) -> None:
+        for k, v in knobs.items():
+            amqft_ragged_tune(self.handle, self.KNOBS.index(k), int(v))
+            self.knobs[k] = int(v)
+
+    def exec(self, x, log2n, offsets, out=None, inverse: bool = False, stream=None):
+        import torch
+
+        for t, dt, name in ((x, torch.complex64, "x"), (log2n, torch.uint8, "log2n"), (offsets, torch.int64, "offsets")):
+            if t.dtype != dt or not t.is_cuda or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous {dt} CUDA tensor")
+        if log2n.numel() != offsets.numel():
+            raise ValueError("log2n and offsets differ in length")
+        if out is None:
+            out = torch.empty_like(x)
+        amqft_exec_ragged(self.handle, log2n.numel(), offsets.data_ptr(), log2n.data_ptr(), x.data_ptr(),
+                          out.data_ptr(), 1 if inverse else 0, _stream_handle(stream))
+        return out
+
+    def skipped(self) -> int:
+        return amqft_ragged_skipped(self.handle)
 
     def close(self):
         if getattr(self, "handle", 0):

@@ -12,7 +12,7 @@
 #include <string>
 
 #include "amqft.h"
-#include "amqft_multipass_impl.cuh"
+#include "amqft_ragged_impl.cuh"
 #include "amqft_internal.h"
 
 namespace amqft {
@@ -25,8 +25,7 @@ FusedConfig fused_config(int logN) {
     c.cluster = 1;
     c.threads = 512;
     // a CTA holds 16384 region values: 512 threads x 32 values
-    const int tpc = (512 * 32) / (N >= 4 ? 2 * N : 8);
-    c.per_cta = tpc < 1 ? 1 : tpc;
+    c.per_cta = small_tpc(logN);
     c.nreg = 4 * c.per_cta;
   } else {
     c.cluster = 4;
@@ -52,6 +51,48 @@ static cudaError_t fused_launch(int variant, const FusedArgs& a, const SmallCons
     default: return launch_variant_8(a, K, c, st);
   }
 }
+
+static cudaError_t ragged_launch(int variant, const FusedArgs& a, const SmallConsts& K, const RaggedArgs& r,
+                                 const RaggedLaunch& L, cudaStream_t st) {
+  switch (variant) {
+    case 1: return ragged_variant_1(a, K, r, L, st);
+    case 2: return ragged_variant_2(a, K, r, L, st);
+    case 3: return ragged_variant_3(a, K, r, L, st);
+    case 4: return ragged_variant_4(a, K, r, L, st);
+    case 5: return ragged_variant_5(a, K, r, L, st);
+    case 6: return ragged_variant_6(a, K, r, L, st);
+    case 7: return ragged_variant_7(a, K, r, L, st);
+    default: return ragged_variant_8(a, K, r, L, st);
+  }
+}
+
+// Bucket pass of a ragged batch: transform ids into one list per log2 N.
+__global__ void ragged_bucket_kernel(const unsigned char* __restrict__ log2n, const long long* __restrict__ off,
+                                     long long count, int maxlog, long long max_points, int* cnt, int* list,
+                                     long long cap, int* skipped, const float2* __restrict__ in,
+                                     float2* __restrict__ out) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int c = log2n[i];
+    if (c > maxlog) {
+      atomicAdd(skipped, 1);
+      continue;
+    }
+    if (c == 0) {  // N = 1: the DFT (and its inverse) is the identity
+      out[off[i]] = in[off[i]];
+      continue;
+    }
+    const int pos = atomicAdd(cnt + c, 1);
+    // multi-pass lengths: the workspace holds max_points >> c transforms
+    const long long capc = c > AMQFT_LOG2N_FUSED_MAX && (max_points >> c) < cap ? (max_points >> c) : cap;
+    if (pos >= capc) {
+      atomicAdd(skipped, 1);
+      continue;
+    }
+    list[c * cap + pos] = (int)i;
+  }
+}
+
 
 static cudaError_t multipass_launch(int variant, const MpArgs& a, float* W0, float* W1, const SmallConsts& K,
                                     cudaStream_t st) {
@@ -156,6 +197,14 @@ struct amqft_plan_s {
   float* d_work;
   long long chunk;
   long long RSg;
+  // ragged plans (amqft_plan_ragged)
+  int ragged;
+  int num_sms;
+  long long max_count, max_points;
+  int* d_rcnt;     // [0, 32) transforms per log2 N, [32] schedule counter, [33] skipped
+  int* d_rlist;    // (log2n + 1) lists of max_count transform ids
+  float* d_rwork;  // multi-pass workspace, shared by the lengths above 2^16 in turn
+  int knob[4];     // schedule, order, small CTAs per SM, cluster grid multiplier
 };
 
 // workspace budget of one plan (both ping-pong buffers)
@@ -231,6 +280,16 @@ int amqft_plan(amqft_plan_t* out, int log2n, int variant, int64_t batch, int dty
   p->d_work = nullptr;
   p->chunk = 0;
   p->RSg = 0;
+  p->ragged = 0;
+  p->num_sms = prop.multiProcessorCount;
+  p->max_count = p->max_points = 0;
+  p->d_rcnt = nullptr;
+  p->d_rlist = nullptr;
+  p->d_rwork = nullptr;
+  p->knob[0] = 1;
+  p->knob[1] = 0;
+  p->knob[2] = 1;
+  p->knob[3] = 1;
   // level-major table: periodisation M = 16..N holds M/8 constants at [M/8-2, M/4-2)
   const long long N = 1LL << log2n;
   const long long ntab = N >= 16 ? N / 4 - 2 : 0;
@@ -305,6 +364,9 @@ static int exec(amqft_plan_t p, const void* in, void* out, int inverse, const in
       a.logN = p->log2n;
       a.inverse = inverse;
       a.RSg = p->RSg;
+      a.tlist = nullptr;
+      a.toff = nullptr;
+      a.ntdev = nullptr;
       e = multipass_launch(p->variant, a, p->d_work, p->d_work + per_buf, p->small, st);
       if (e != cudaSuccess) return cuda_fail(e, "multi-pass launch");
     }
@@ -332,6 +394,8 @@ static int exec(amqft_plan_t p, const void* in, void* out, int inverse, const in
   a.inverse = inverse;
   a.RS = p->cfg.RS;
   a.tot_off = p->cfg.tot_off;
+  a.tlist = nullptr;
+  a.toff = nullptr;
   e = fused_launch(p->variant, a, p->small, p->cfg, st);
   if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
   return AMQFT_OK;
@@ -351,7 +415,151 @@ int amqft_destroy(amqft_plan_t p) {
   if (!p) return AMQFT_OK;
   if (p->d_ctab) cudaFree(p->d_ctab);
   if (p->d_work) cudaFree(p->d_work);
+  if (p->d_rcnt) cudaFree(p->d_rcnt);
+  if (p->d_rlist) cudaFree(p->d_rlist);
+  if (p->d_rwork) cudaFree(p->d_rwork);
   delete p;
+  return AMQFT_OK;
+}
+
+static long long ragged_capacity(const amqft_plan_s* p, int c) {
+  const long long byp = p->max_points >> c;
+  return byp < p->max_count ? byp : p->max_count;
+}
+
+static long long region_stride_g(int c) { return (((1LL << (c - 1)) + 2 + 31) / 32) * 32; }
+
+int amqft_plan_ragged(amqft_plan_t* out, int max_log2n, int variant, int dtype, int64_t max_count,
+                      int64_t max_points) {
+  t_err.clear();
+  if (!out) return fail(AMQFT_ERR_ARG, "amqft_plan_ragged: out is NULL");
+  *out = nullptr;
+  if (dtype != AMQFT_C64) return fail(AMQFT_ERR_DTYPE, "amqft_plan_ragged: ragged batches are AMQFT_C64 only");
+  if (max_count < 1 || max_count > (1LL << 30))
+    return fail(AMQFT_ERR_ARG, "amqft_plan_ragged: max_count=%lld outside [1, 2^30]", (long long)max_count);
+  if (max_points < 1) return fail(AMQFT_ERR_ARG, "amqft_plan_ragged: max_points=%lld < 1", (long long)max_points);
+  amqft_plan_t p = nullptr;
+  int rc = amqft_plan(&p, max_log2n, variant, 0, dtype);
+  if (rc != AMQFT_OK) return rc;
+  p->ragged = 1;
+  p->max_count = max_count;
+  p->max_points = max_points;
+  cudaError_t e = cudaMalloc(&p->d_rcnt, 64 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_rlist, (size_t)(max_log2n + 1) * (size_t)max_count * sizeof(int));
+  long long ws = 0;
+  for (int c = AMQFT_LOG2N_FUSED_MAX + 1; c <= max_log2n; ++c) {
+    const long long need = 2LL * ragged_capacity(p, c) * 4 * region_stride_g(c);
+    if (need > ws) ws = need;
+  }
+  if (e == cudaSuccess && ws > 0) e = cudaMalloc(&p->d_rwork, (size_t)ws * sizeof(float));
+  if (e != cudaSuccess) {
+    amqft_destroy(p);
+    return fail(AMQFT_ERR_NOMEM, "amqft_plan_ragged: device allocation failed: %s", cudaGetErrorString(e));
+  }
+  *out = p;
+  return AMQFT_OK;
+}
+
+int amqft_exec_ragged(amqft_plan_t p, int64_t count, const int64_t* d_offsets, const uint8_t* d_log2n,
+                      const void* in, void* out, int direction, void* stream) {
+  t_err.clear();
+  if (!p) return fail(AMQFT_ERR_ARG, "plan is NULL");
+  if (!p->ragged) return fail(AMQFT_ERR_ARG, "amqft_exec_ragged: the plan was not made by amqft_plan_ragged");
+  if (count < 0 || count > p->max_count)
+    return fail(AMQFT_ERR_ARG, "amqft_exec_ragged: count=%lld outside [0, max_count=%lld]", (long long)count,
+                p->max_count);
+  if (direction != 0 && direction != 1) return fail(AMQFT_ERR_ARG, "amqft_exec_ragged: direction must be 0 or 1");
+  if (count == 0) return AMQFT_OK;
+  if (!in || !out || !d_offsets || !d_log2n) return fail(AMQFT_ERR_ALIGN, "amqft_exec_ragged: NULL pointer");
+  if ((((uintptr_t)in | (uintptr_t)out | (uintptr_t)d_offsets) & 7u) != 0)
+    return fail(AMQFT_ERR_ALIGN, "amqft_exec_ragged: in, out and offsets must be 8-byte aligned");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e = cudaMemsetAsync(p->d_rcnt, 0, 64 * sizeof(int), st);
+  if (e != cudaSuccess) return cuda_fail(e, "amqft_exec_ragged: cudaMemsetAsync");
+  {
+    long long blocks = (count + 255) / 256;
+    if (blocks > 8LL * p->num_sms) blocks = 8LL * p->num_sms;
+    ragged_bucket_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_log2n, (const long long*)d_offsets, count, p->log2n,
+                                                           p->max_points, p->d_rcnt, p->d_rlist, p->max_count,
+                                                           p->d_rcnt + 33, (const float2*)in, (float2*)out);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "ragged bucket launch");
+  }
+  FusedArgs a;
+  memset(&a, 0, sizeof a);
+  a.in = in;
+  a.out = out;
+  a.dtype = AMQFT_C64;
+  a.ctab = p->d_ctab;
+  a.inverse = direction;
+  a.toff = (const long long*)d_offsets;
+  RaggedArgs r;
+  r.cnt = p->d_rcnt;
+  r.list = p->d_rlist;
+  r.cap = p->max_count;
+  r.work = p->d_rcnt + 32;
+  r.maxlog = p->log2n < AMQFT_LOG2N_FUSED_MAX ? p->log2n : AMQFT_LOG2N_FUSED_MAX;
+  r.sched = p->knob[0];
+  r.order = p->knob[1];
+  RaggedLaunch L;
+  memset(&L, 0, sizeof L);
+  L.small_grid = p->num_sms * p->knob[2];
+  for (int c = 1; c <= 13 && c <= r.maxlog; ++c) {
+    const int tpc = small_tpc(c);
+    const int sm_bytes =
+        (small_tot_off(c) + 512 + 32 + snap_floats(4 * tpc * (1 << (c - 1)))) * (int)sizeof(float);
+    if (sm_bytes > L.small_smem) L.small_smem = sm_bytes;
+  }
+  for (int q = 0; q < 3; ++q) {
+    const FusedConfig fc = fused_config(14 + q);
+    L.clusters[q] = (p->num_sms / 4) * p->knob[3];
+    L.cluster_smem[q] = fc.smem;
+    L.cluster_tot_off[q] = fc.tot_off;
+  }
+  e = ragged_launch(p->variant, a, p->small, r, L, st);
+  if (e != cudaSuccess) return cuda_fail(e, "ragged launch");
+  for (int c = AMQFT_LOG2N_FUSED_MAX + 1; c <= p->log2n; ++c) {
+    const long long capc = ragged_capacity(p, c);
+    if (capc < 1) continue;
+    const long long RSg = region_stride_g(c);
+    MpArgs m;
+    memset(&m, 0, sizeof m);
+    m.in = in;
+    m.out = out;
+    m.dtype = AMQFT_C64;
+    m.ctab = p->d_ctab;
+    m.nt = capc;
+    m.t0 = 0;
+    m.logN = c;
+    m.inverse = direction;
+    m.RSg = RSg;
+    m.tlist = p->d_rlist + (long long)c * p->max_count;
+    m.toff = (const long long*)d_offsets;
+    m.ntdev = p->d_rcnt + c;
+    e = multipass_launch(p->variant, m, p->d_rwork, p->d_rwork + capc * 4 * RSg, p->small, st);
+    if (e != cudaSuccess) return cuda_fail(e, "ragged multi-pass launch");
+  }
+  return AMQFT_OK;
+}
+
+int amqft_ragged_tune(amqft_plan_t p, int knob, int value) {
+  t_err.clear();
+  if (!p || !p->ragged) return fail(AMQFT_ERR_ARG, "amqft_ragged_tune: not a ragged plan");
+  static const int lo[4] = {0, 0, 1, 1}, hi[4] = {1, 1, 4, 4};
+  if (knob < 0 || knob > 3) return fail(AMQFT_ERR_ARG, "amqft_ragged_tune: knob=%d not in 0..3", knob);
+  if (value < lo[knob] || value > hi[knob])
+    return fail(AMQFT_ERR_ARG, "amqft_ragged_tune: value %d for knob %d outside [%d, %d]", value, knob, lo[knob],
+                hi[knob]);
+  p->knob[knob] = value;
+  return AMQFT_OK;
+}
+
+int amqft_ragged_skipped(amqft_plan_t p, int64_t* skipped) {
+  t_err.clear();
+  if (!p || !p->ragged || !skipped) return fail(AMQFT_ERR_ARG, "amqft_ragged_skipped: bad arguments");
+  int v = 0;
+  const cudaError_t e = cudaMemcpy(&v, p->d_rcnt + 33, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "amqft_ragged_skipped: cudaMemcpy");
+  *skipped = v;
   return AMQFT_OK;
 }
 

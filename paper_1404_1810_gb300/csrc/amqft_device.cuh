@@ -71,6 +71,8 @@ struct FusedArgs {
   int inverse;         // 1: conj in / conj out
   int RS;              // region stride in floats
   int tot_off;         // float offset of the scan scratch in shared memory
+  const int* tlist;    // transform ids by list position (NULL: the position itself)
+  const long long* toff;  // element offset of each transform id (NULL: id * N)
 };
 
 template <int V>
@@ -535,7 +537,12 @@ __device__ __noinline__ void run_leaf(float* R, int p0, int ctx, const SmallCons
 // multi-pass path).
 struct Geo {
   int logN, half, RS, nreg, gbase, sub;
+  int nreg_cap;  // regions a full CTA holds: fixes the scan chunking, so a
+                 // transform's rounding does not depend on its batch neighbours
 };
+
+// Transforms per CTA of the single-CTA path (N <= 2^13): 16384 region values.
+__host__ __device__ constexpr int small_tpc(int logN) { return (512 * 32) / ((1 << logN) >= 4 ? 2 * (1 << logN) : 8); }
 
 // context of region (or node) r: region mode, C1 S1 C2 S2 alternate DCT/DST;
 // node mode, gbase is a bit mask of the nodes' root contexts
@@ -731,8 +738,9 @@ __device__ __forceinline__ void pass_recurrence(float* sm, float* tot, float* ws
   const int Lp = 1 << logLp, H = Lp >> 1, h = logLp - 1;
   const unsigned nb = nodes_at(g, logLp);
   const unsigned total = nb * (unsigned)H * (unsigned)g.nreg;
+  const unsigned total_cap = nb * (unsigned)H * (unsigned)g.nreg_cap;
   int logC = 1;
-  while (((unsigned)TPB << logC) < total) ++logC;
+  while (((unsigned)TPB << logC) < total_cap) ++logC;
   const int C = 1 << logC, logSC = h - logC, SC = 1 << logSC;
   const unsigned nch = total >> logC;
   const Div dv(nb);

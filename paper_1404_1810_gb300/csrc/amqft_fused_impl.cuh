@@ -99,10 +99,11 @@ struct Fetched {
   float2 a, b, c, d;
 };
 
-__device__ __forceinline__ Fetched load_fetch(const InRef& in, int logN, long long t, int n, float cj) {
+// t: transform id (indexes the exponents), off: element offset of its data
+__device__ __forceinline__ Fetched load_fetch(const InRef& in, int logN, long long t, long long off, int n, float cj) {
   const int N = 1 << logN, half = N >> 1, Q = N >> 2;
-  const float2* __restrict__ z = static_cast<const float2*>(in.p) + t * (long long)N;
-  const unsigned* __restrict__ z16 = static_cast<const unsigned*>(in.p) + t * (long long)N;
+  const float2* __restrict__ z = static_cast<const float2*>(in.p) + off;
+  const unsigned* __restrict__ z16 = static_cast<const unsigned*>(in.p) + off;
   const bool c64 = in.dtype == DT_C64;  // the same for every thread
   const float s = (!c64 && in.exp) ? pow2f(__ldg(in.exp + t)) : 1.f;
   auto ld = [&](int i) { return c64 ? ldz(z, i, cj) : ldz16(z16, i, in.dtype, s, cj); };
@@ -279,19 +280,19 @@ __device__ __forceinline__ float out4_absmax(const Out4& o) {
 }
 
 template <int V>
-__device__ __forceinline__ void store_emit(float2* __restrict__ out, int logN, long long t, int k, const Gathered& g,
+__device__ __forceinline__ void store_emit(float2* __restrict__ out, int logN, long long off, int k, const Gathered& g,
                                            float cj) {
   const Out4 o = emit_values<V>(logN, k, g);
-  float2* __restrict__ z = out + t * (long long)(1 << logN);
+  float2* __restrict__ z = out + off;
 #pragma unroll
   for (int j = 0; j < 4; ++j)
     if (o.i[j] >= 0) stz(z, o.i[j], o.v[j].x, o.v[j].y, cj);
 }
 
 // 16-bit output of one item, every value times s = 2^-exp (exact)
-__device__ __forceinline__ void store16(unsigned* __restrict__ out, int logN, long long t, const Out4& o, float s,
-                                        float cj, int dtype) {
-  unsigned* __restrict__ z = out + t * (long long)(1 << logN);
+__device__ __forceinline__ void store16(unsigned* __restrict__ out, long long off, const Out4& o, float s, float cj,
+                                        int dtype) {
+  unsigned* __restrict__ z = out + off;
 #pragma unroll
   for (int j = 0; j < 4; ++j)
     if (o.i[j] >= 0) __stcs(z + o.i[j], pack16(o.v[j].x * s, o.v[j].y * (s * cj), dtype));
@@ -379,8 +380,8 @@ __device__ __forceinline__ void region_to_natural(float* R, int ctx) {
 //   X(0) = (C1(0), C2(0)),  X(N/2) = (C1(N/2), C2(N/2)).
 // CTA r of the cluster (region r) covers k in [r N/8, (r+1) N/8).
 template <int TPB, int LN>
-__device__ __forceinline__ void store_natural_cluster(float* sm, const FusedArgs& a, long long t, float cj,
-                                                      float* red) {
+__device__ __forceinline__ void store_natural_cluster(float* sm, const FusedArgs& a, long long t, long long off,
+                                                      float cj, float* red) {
   constexpr int N = 1 << LN, half = N >> 1, PER = half / 4, NG = PER / 4 / TPB;
   static_assert(NG * 4 * TPB == PER, "four harmonics per thread and step");
   cg::cluster_group cl = cg::this_cluster();
@@ -407,8 +408,8 @@ __device__ __forceinline__ void store_natural_cluster(float* sm, const FusedArgs
     return k0;
   };
   if (a.dtype == DT_C64) {
-    float2* __restrict__ z = static_cast<float2*>(a.out) + t * (long long)N;
-    const bool vec_ok = (reinterpret_cast<uintptr_t>(a.out) & 15u) == 0;  // same for every thread
+    float2* __restrict__ z = static_cast<float2*>(a.out) + off;
+    const bool vec_ok = (reinterpret_cast<uintptr_t>(z) & 15u) == 0;  // same for every thread
 #pragma unroll
     for (int gi = 0; gi < NG; ++gi) {
       float2 f[4], b[4];
@@ -452,8 +453,8 @@ __device__ __forceinline__ void store_natural_cluster(float* sm, const FusedArgs
   const int e = block_exponent(M);
   const float sc = pow2f(-e), si = sc * cj;
   if (rank == 0 && threadIdx.x == 0) a.exp_out[t] = e;
-  unsigned* __restrict__ z = static_cast<unsigned*>(a.out) + t * (long long)N;
-  const bool vec_ok = (reinterpret_cast<uintptr_t>(a.out) & 15u) == 0;
+  unsigned* __restrict__ z = static_cast<unsigned*>(a.out) + off;
+  const bool vec_ok = (reinterpret_cast<uintptr_t>(z) & 15u) == 0;
 #pragma unroll
   for (int gi = 0; gi < NG; ++gi) {
     float2 f[4], b[4];
@@ -473,13 +474,18 @@ __device__ __forceinline__ void store_natural_cluster(float* sm, const FusedArgs
   }
 }
 
-// LN > 0: the kernel is compiled for log2 N = LN (every index computation
-// is then resolved at compile time); LN == 0: a.logN at run time.
+// The fused transform of the CTA (cluster size 1: transforms at list
+// positions [j0, j0 + ntr)) or of the cluster (list position j0).  LN > 0:
+// compiled for log2 N = LN (every index computation is then resolved at
+// compile time); LN == 0: a.logN at run time.
+// logN_rt, RS_rt: the length and region stride when LN == 0; tot_off: float
+// offset of the scan scratch; tlist: transform ids by list position (NULL:
+// the position itself).  Everything else comes from a.
 template <int V, int TPB, int MAXI, int CL, int LN>
-__global__ void __launch_bounds__(TPB) fused_kernel(const FusedArgs a, const __grid_constant__ SmallConsts K) {
-  extern __shared__ __align__(16) float sm[];
-  const int logN = LN > 0 ? LN : a.logN, N = 1 << logN, half = N >> 1;
-  const int RS = LN > 0 ? region_stride(LN) : a.RS;
+__device__ __forceinline__ void fused_body(const FusedArgs& a, const SmallConsts& K, float* sm, long long j0, int ntr,
+                                           int logN_rt, int RS_rt, int tot_off, const int* tlist) {
+  const int logN = LN > 0 ? LN : logN_rt, N = 1 << logN, half = N >> 1;
+  const int RS = LN > 0 ? region_stride(LN) : RS_rt;
   const int Qi = N >= 4 ? (N >> 2) : 1;   // orbit items per transform
   const int logQi = N >= 4 ? logN - 2 : 0;
   const float cj = a.inverse ? -1.f : 1.f;
@@ -491,22 +497,25 @@ __global__ void __launch_bounds__(TPB) fused_kernel(const FusedArgs a, const __g
   Regions<CL> rg;
   rg.sm = sm;
   rg.RS = RS;
-  int ntr;
+  rg.tbase = j0;
+  // transform id of local transform tau, and the element offset of an id
+  auto tid = [&](int tau) -> long long {
+    const long long j = j0 + tau;
+    return tlist ? (long long)__ldg(tlist + j) : j;
+  };
+  auto toff = [&](long long t) -> long long { return a.toff ? __ldg(a.toff + t) : (t << logN); };
   if constexpr (CL == 1) {
-    rg.tbase = (long long)blockIdx.x * a.tpc;
-    const long long left = a.batch - rg.tbase;
-    ntr = left < a.tpc ? (int)left : a.tpc;
     g.nreg = 4 * ntr;
+    g.nreg_cap = 4 * small_tpc(logN);
     g.gbase = 0;
   } else {
     cg::cluster_group cl = cg::this_cluster();
-    rg.tbase = blockIdx.x / CL;
-    ntr = 1;
     g.nreg = 4 / CL;
+    g.nreg_cap = 4 / CL;
     g.gbase = (int)cl.block_rank() * (4 / CL);
-    cl.sync();  // every CTA of the cluster is resident before remote writes
+    cl.sync();  // every CTA of the cluster is resident (and done with the previous transform)
   }
-  float* tot = sm + a.tot_off;
+  float* tot = sm + tot_off;
   float* wsum = tot + TPB;
   float* snap = wsum + 32;
 
@@ -530,7 +539,10 @@ __global__ void __launch_bounds__(TPB) fused_kernel(const FusedArgs a, const __g
         n_[s] = (int)cg::this_cluster().block_rank() * per + threadIdx.x + s * TPB;
         ok_[s] = (int)threadIdx.x + s * TPB < per;
       }
-      if (ok_[s]) f_[s] = load_fetch(InRef{a.in, a.exp_in, a.dtype}, logN, rg.tbase + tau_[s], n_[s], cj);
+      if (ok_[s]) {
+        const long long t = tid(tau_[s]);
+        f_[s] = load_fetch(InRef{a.in, a.exp_in, a.dtype}, logN, t, toff(t), n_[s], cj);
+      }
     }
 #pragma unroll
     for (int s = 0; s < NIT; ++s)
@@ -615,7 +627,8 @@ __global__ void __launch_bounds__(TPB) fused_kernel(const FusedArgs a, const __g
     __syncthreads();
     region_to_natural<V, TPB, LN>(sm, (int)cg::this_cluster().block_rank() & 1);
     cg::this_cluster().sync();
-    store_natural_cluster<TPB, LN>(sm, a, rg.tbase, cj, tot);
+    const long long t = tid(0);
+    store_natural_cluster<TPB, LN>(sm, a, t, toff(t), cj, tot);
     cg::this_cluster().sync();  // keep shared memory alive for the other CTAs' reads
     return;
   }
@@ -642,7 +655,7 @@ __global__ void __launch_bounds__(TPB) fused_kernel(const FusedArgs a, const __g
     if (a.dtype == DT_C64) {
 #pragma unroll
       for (int s = 0; s < 4; ++s)
-        if (ok_[s]) store_emit<V>(static_cast<float2*>(a.out), logN, rg.tbase + tau_[s], k_[s], g_[s], cj);
+        if (ok_[s]) store_emit<V>(static_cast<float2*>(a.out), logN, toff(tid(tau_[s])), k_[s], g_[s], cj);
     } else {
       // 16-bit: one exponent per transform from its largest component
       static_assert(CL == 1 || LN > 0, "the cluster path stores through store_natural_cluster");
@@ -662,13 +675,27 @@ __global__ void __launch_bounds__(TPB) fused_kernel(const FusedArgs a, const __g
       for (int s = 0; s < 4; ++s) {
         if (ok_[s]) {
           const int e = block_exponent(__int_as_float(slot[tau_[s]]));
-          store16(static_cast<unsigned*>(a.out), logN, rg.tbase + tau_[s], o_[s], pow2f(-e), cj, a.dtype);
-          if (k_[s] == 0) a.exp_out[rg.tbase + tau_[s]] = e;
+          const long long t = tid(tau_[s]);
+          store16(static_cast<unsigned*>(a.out), toff(t), o_[s], pow2f(-e), cj, a.dtype);
+          if (k_[s] == 0) a.exp_out[t] = e;
         }
       }
     }
   }
   if constexpr (CL > 1) cg::this_cluster().sync();  // keep shared memory alive for the other CTAs' reads
+}
+
+template <int V, int TPB, int MAXI, int CL, int LN>
+__global__ void __launch_bounds__(TPB) fused_kernel(const FusedArgs a, const __grid_constant__ SmallConsts K) {
+  extern __shared__ __align__(16) float sm[];
+  if constexpr (CL == 1) {
+    const long long j0 = (long long)blockIdx.x * a.tpc;
+    const long long left = a.batch - j0;
+    fused_body<V, TPB, MAXI, CL, LN>(a, K, sm, j0, left < a.tpc ? (int)left : a.tpc, a.logN, a.RS, a.tot_off,
+                                     a.tlist);
+  } else {
+    fused_body<V, TPB, MAXI, CL, LN>(a, K, sm, (long long)(blockIdx.x / CL), 1, LN, 0, a.tot_off, a.tlist);
+  }
 }
 
 // ---------------------------------------------------------------------

@@ -1,9 +1,13 @@
 // Fused AM-QFT kernels of variant 3 (instantiated in a translation unit of
 // their own so the eight variants compile in parallel).
-#include "amqft_fused_impl.cuh"
+#include "amqft_ragged_impl.cuh"
 
 namespace amqft {
 cudaError_t launch_variant_3(const FusedArgs& a, const SmallConsts& K, const FusedConfig& c, cudaStream_t st) {
   return launch_v<3>(a, K, c, st);
+}
+cudaError_t ragged_variant_3(const FusedArgs& a, const SmallConsts& K, const RaggedArgs& r, const RaggedLaunch& L,
+                               cudaStream_t st) {
+  return ragged_run<3>(a, K, r, L, st);
 }
 }  // namespace amqft

@@ -1,6 +1,6 @@
 // Fused AM-QFT kernels of variant 4 (instantiated in a translation unit of
 // their own so the eight variants compile in parallel).
-#include "amqft_multipass_impl.cuh"
+#include "amqft_ragged_impl.cuh"
 
 namespace amqft {
 cudaError_t launch_variant_4(const FusedArgs& a, const SmallConsts& K, const FusedConfig& c, cudaStream_t st) {
@@ -8,5 +8,9 @@ cudaError_t launch_variant_4(const FusedArgs& a, const SmallConsts& K, const Fus
 }
 cudaError_t multipass_variant_4(const MpArgs& a, float* W0, float* W1, const SmallConsts& K, cudaStream_t st) {
   return mp_run<4>(a, W0, W1, K, st);
+}
+cudaError_t ragged_variant_4(const FusedArgs& a, const SmallConsts& K, const RaggedArgs& r, const RaggedLaunch& L,
+                               cudaStream_t st) {
+  return ragged_run<4>(a, K, r, L, st);
 }
 }  // namespace amqft

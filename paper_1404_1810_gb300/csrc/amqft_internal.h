@@ -10,6 +10,8 @@ namespace amqft {
 struct FusedArgs;
 struct SmallConsts;
 struct MpArgs;
+struct RaggedArgs;
+struct RaggedLaunch;
 
 // Launch shape of the fused kernel for one transform length.
 struct FusedConfig {
@@ -32,6 +34,16 @@ cudaError_t launch_variant_5(const FusedArgs&, const SmallConsts&, const FusedCo
 cudaError_t launch_variant_6(const FusedArgs&, const SmallConsts&, const FusedConfig&, cudaStream_t);
 cudaError_t launch_variant_7(const FusedArgs&, const SmallConsts&, const FusedConfig&, cudaStream_t);
 cudaError_t launch_variant_8(const FusedArgs&, const SmallConsts&, const FusedConfig&, cudaStream_t);
+
+// ragged batches (every length up to the plan's), all variants
+cudaError_t ragged_variant_1(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t);
+cudaError_t ragged_variant_2(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t);
+cudaError_t ragged_variant_3(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t);
+cudaError_t ragged_variant_4(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t);
+cudaError_t ragged_variant_5(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t);
+cudaError_t ragged_variant_6(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t);
+cudaError_t ragged_variant_7(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t);
+cudaError_t ragged_variant_8(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t);
 
 // multi-pass path (2^17 <= N <= 2^24), variants 2, 4, 6, 8
 cudaError_t multipass_variant_2(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t);

@@ -39,7 +39,24 @@ struct MpArgs {
   int logN;
   int inverse;
   long long RSg;      // region stride in the workspace (floats)
+  const int* tlist;   // transform ids of chunk positions (NULL: t0 + position)
+  const long long* toff;  // element offset of each transform id (NULL: id * N)
+  const int* ntdev;   // transforms in this chunk, read on the device (NULL: nt); nt is then the capacity
 };
+
+__device__ __forceinline__ long long mp_nt(const MpArgs& a) {
+  if (!a.ntdev) return a.nt;
+  const long long n = (long long)*a.ntdev;  // written by an earlier kernel of the stream
+  return n < a.nt ? n : a.nt;
+}
+
+// transform id of chunk position t, and the element offset of an id
+__device__ __forceinline__ long long mp_id(const MpArgs& a, long long t) {
+  return a.tlist ? (long long)__ldg(a.tlist + t) : a.t0 + t;
+}
+__device__ __forceinline__ long long mp_off(const MpArgs& a, long long id) {
+  return a.toff ? __ldg(a.toff + id) : (id << a.logN);
+}
 
 struct GRegions {
   float* W;
@@ -50,13 +67,14 @@ struct GRegions {
 template <int V>
 __global__ void mp_load_kernel(MpArgs a, float* W) {
   const int logQ = a.logN - 2;
-  const long long total = a.nt << logQ;
+  const long long total = mp_nt(a) << logQ;
   const float cj = a.inverse ? -1.f : 1.f;
   GRegions rg{W, a.RSg};
   for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
     const long long t = w >> logQ;
     const int n = (int)(w & ((1LL << logQ) - 1));
-    const Fetched f = load_fetch(InRef{a.in, a.exp_in, a.dtype}, a.logN, a.t0 + t, n, cj);
+    const long long id = mp_id(a, t);
+    const Fetched f = load_fetch(InRef{a.in, a.exp_in, a.dtype}, a.logN, id, mp_off(a, id), n, cj);
     load_scatter<V>(rg, a.logN, (int)t, n, f);
   }
 }
@@ -64,14 +82,14 @@ __global__ void mp_load_kernel(MpArgs a, float* W) {
 template <int V>
 __global__ void mp_store_kernel(MpArgs a, const float* W) {
   const int logQ = a.logN - 2;
-  const long long total = a.nt << logQ;
+  const long long total = mp_nt(a) << logQ;
   const float cj = a.inverse ? -1.f : 1.f;
   GRegions rg{const_cast<float*>(W), a.RSg};
   for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
     const long long t = w >> logQ;
     const int k = (int)(w & ((1LL << logQ) - 1));
     const Gathered g = store_gather<V>(rg, a.logN, (int)t, k);
-    store_emit<V>(static_cast<float2*>(a.out), a.logN, a.t0 + t, k, g, cj);
+    store_emit<V>(static_cast<float2*>(a.out), a.logN, mp_off(a, mp_id(a, t)), k, g, cj);
   }
 }
 
@@ -80,7 +98,7 @@ __global__ void mp_store_kernel(MpArgs a, const float* W) {
 template <int V>
 __global__ void mp_max_kernel(MpArgs a, const float* W, int* Mx) {
   const int logQ = a.logN - 2;
-  const long long total = a.nt << logQ;
+  const long long total = mp_nt(a) << logQ;
   GRegions rg{const_cast<float*>(W), a.RSg};
   for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
     const long long t = w >> logQ;
@@ -101,7 +119,7 @@ __global__ void mp_zero_kernel(int* Mx, long long n) {
 template <int V>
 __global__ void mp_store16_kernel(MpArgs a, const float* W, const int* Mx) {
   const int logQ = a.logN - 2;
-  const long long total = a.nt << logQ;
+  const long long total = mp_nt(a) << logQ;
   const float cj = a.inverse ? -1.f : 1.f;
   GRegions rg{const_cast<float*>(W), a.RSg};
   for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
@@ -109,8 +127,9 @@ __global__ void mp_store16_kernel(MpArgs a, const float* W, const int* Mx) {
     const int k = (int)(w & ((1LL << logQ) - 1));
     const Out4 o = emit_values<V>(a.logN, k, store_gather<V>(rg, a.logN, (int)t, k));
     const int e = block_exponent(__int_as_float(Mx[t]));
-    store16(static_cast<unsigned*>(a.out), a.logN, a.t0 + t, o, pow2f(-e), cj, a.dtype);
-    if (k == 0) a.exp_out[a.t0 + t] = e;
+    const long long id = mp_id(a, t);
+    store16(static_cast<unsigned*>(a.out), mp_off(a, id), o, pow2f(-e), cj, a.dtype);
+    if (k == 0) a.exp_out[id] = e;
   }
 }
 
@@ -121,7 +140,7 @@ __global__ void mp_quartet_kernel(MpArgs a, float* W, int logLp) {
   const int half = 1 << (a.logN - 1), logQ = logLp - 2;
   const long long nb = (half >> logLp) - 1;
   const long long per = nb << logQ;
-  const long long total = per * 4 * a.nt;
+  const long long total = per * 4 * mp_nt(a);
   for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
     const long long rr = w / per, rem = w - rr * per;
     float* R = W + rr * a.RSg;
@@ -139,7 +158,7 @@ __global__ void mp_quartet_kernel(MpArgs a, float* W, int logLp) {
 template <int V>
 __global__ void mp_neighbour_kernel(MpArgs a, const float* __restrict__ Win, float* __restrict__ Wout, int logLp) {
   const int half = 1 << (a.logN - 1), Lp = 1 << logLp, H = Lp >> 1, h = logLp - 1;
-  const long long total = a.RSg * 4 * a.nt;
+  const long long total = a.RSg * 4 * mp_nt(a);
   for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
     const long long rr = w / a.RSg;
     const int ph = (int)(w - rr * a.RSg);  // physical (swizzled) word
@@ -175,7 +194,7 @@ __global__ void mp_neighbour_kernel(MpArgs a, const float* __restrict__ Win, flo
 template <int V>
 __global__ void mp_chain_kernel(MpArgs a, const float* __restrict__ Win, float* __restrict__ Wout, int logM) {
   const int half = 1 << (a.logN - 1), M = 1 << logM, logQ = logM - 2, Q = 1 << logQ, P = half - M / 2;
-  const long long total = a.RSg * 4 * a.nt;
+  const long long total = a.RSg * 4 * mp_nt(a);
   for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
     const long long rr = w / a.RSg;
     const int ph = (int)(w - rr * a.RSg);
@@ -237,6 +256,7 @@ __global__ void __launch_bounds__(TPB) mp_solve_kernel(MpArgs a, float* W, const
   const int nnode = (half >> MP_LOG_S) - 2;  // nodes of size S in [0, half - 2S)
   const int per = nnode / 2 + 1;
   const long long rr = blockIdx.x / per;
+  if (rr >= 4 * mp_nt(a)) return;  // launched for the capacity (uniform per block, before any barrier)
   const int sidx = (int)(blockIdx.x - rr * per);
   float* R = W + rr * a.RSg;
   const int ctx0 = (int)(rr & 1);
@@ -258,6 +278,7 @@ __global__ void __launch_bounds__(TPB) mp_solve_kernel(MpArgs a, float* W, const
     g.half = MP_S;
     g.RS = RSn;
     g.nreg = 2;
+    g.nreg_cap = 2;
     g.gbase = mask;
     g.sub = MP_S;
     __syncthreads();
@@ -306,6 +327,7 @@ __global__ void __launch_bounds__(TPB) mp_solve_kernel(MpArgs a, float* W, const
     g.half = halfp;
     g.RS = words;
     g.nreg = 1;
+    g.nreg_cap = 1;
     g.gbase = ctx0;
     g.sub = 0;
     __syncthreads();

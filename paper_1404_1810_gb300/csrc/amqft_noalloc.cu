@@ -124,6 +124,9 @@ extern "C" int amqft_exec_static(amqft_plan_t plan, int64_t batch, const void* i
     a.logN = pv.log2n;
     a.inverse = inverse ? 1 : 0;
     a.RSg = RSg;
+    a.tlist = nullptr;
+    a.toff = nullptr;
+    a.ntdev = nullptr;
     e = multipass_dispatch(pv.variant, a, scratch, scratch + chunk * 4 * RSg, *pv.small, st);
     if (e != cudaSuccess)
       return set_error(AMQFT_ERR_CUDA, "amqft_exec_static: multi-pass launch: %s", cudaGetErrorString(e));

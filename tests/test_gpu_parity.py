@@ -216,3 +216,16 @@ def test_output_only_8_byte_aligned(v, log2n):
         assert torch.equal(buf[1:].reshape(b, n), ref_i)
     finally:
         p.close()
+
+
+@pytest.mark.parametrize("v", [1, 3, 5, 7])
+@pytest.mark.parametrize("log2n", [8, 10, 13])
+def test_result_independent_of_batch_neighbours(v, log2n):
+    """A transform gives the same bits alone, in a full CTA and in a partial
+    one (the recurrence variants' scan chunking follows the CTA capacity)."""
+    n = 1 << log2n
+    x = synth.normal_complex(n, 11, config=2, stream=600 + log2n)
+    alone = run_gpu(x[3:4], v)
+    for b in (4, 7, 11):
+        batch = run_gpu(x[:b], v)
+        assert np.array_equal(batch[3], alone[0]), (v, log2n, b)

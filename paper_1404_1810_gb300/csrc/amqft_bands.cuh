@@ -146,18 +146,21 @@ __device__ __forceinline__ void fold_bundle(float* Rg, int half, int logL, int i
   }
 }
 
-// A fold band over every region of the CTA.  Work groups: item pairs of the
+// A fold band over every region of the CTA (GRID: of the whole grid, the
+// regions then living in global memory).  Work groups: item pairs of the
 // class-0 nodes (size L, blocks [0, half - L)), then pairs of the bundle.
-template <int V, bool FWD, int R, int TPB>
+template <int V, bool FWD, int R, int TPB, bool GRID = false>
 __device__ __forceinline__ void run_fold_band(float* sm, const Geo& g, int logL, const float* __restrict__ ctab) {
   const int logW = logL - R, W2 = 1 << (logW - 1);
   const unsigned nb0 = nodes_at(g, logL);
   const unsigned per = (nb0 + (g.sub ? 0u : 1u)) << (logW - 1);  // groups per region (+ bundle)
   const unsigned total = per * (unsigned)g.nreg;
   const Div dv(per);
-  for (unsigned w = threadIdx.x; w < total; w += TPB) {
+  const unsigned start = GRID ? blockIdx.x * TPB + threadIdx.x : threadIdx.x;
+  const unsigned stride = GRID ? gridDim.x * TPB : TPB;
+  for (unsigned w = start; w < total; w += stride) {
     const unsigned r = dv(w), gidx = w - r * per;
-    float* Rg = sm + r * g.RS;
+    float* Rg = sm + (long long)r * g.RS;
     const int c0 = ctx_of(g, r);
     const unsigned b = gidx >> (logW - 1);
     const int i = (int)(gidx & (unsigned)(W2 - 1));
@@ -300,7 +303,7 @@ __device__ __forceinline__ void run_chunk_band(float* sm, float* snap, const Geo
   for (unsigned w = threadIdx.x; w < total; w += TPB) {
     if (lane != 0 && lane != 31) continue;
     const unsigned r = dv(w), it = w - r * per;
-    const float* Rg = sm + r * g.RS;
+    const float* Rg = sm + (long long)r * g.RS;
     const int c0 = ctx_of(g, r);
     const unsigned b = it >> logW;
     const int q = (int)(it & (unsigned)(W - 1)), m = q;
@@ -318,7 +321,7 @@ __device__ __forceinline__ void run_chunk_band(float* sm, float* snap, const Geo
   // pass 2: in place
   for (unsigned w = threadIdx.x; w < total; w += TPB) {
     const unsigned r = dv(w), it = w - r * per;
-    float* Rg = sm + r * g.RS;
+    float* Rg = sm + (long long)r * g.RS;
     const int c0 = ctx_of(g, r);
     const unsigned b = it >> logW;
     const int m = (int)(it & (unsigned)(W - 1));
@@ -364,16 +367,17 @@ __device__ __forceinline__ void run_chunk_band_r(float* sm, float* snap, const G
 }
 
 // Band plan: pass levels (node sizes N/4 .. 2*LEAF) split into bands of at
-// most RMAX levels, as even as possible, the top band first.
+// most RMAX levels, as even as possible, the top band first.  The multi-pass
+// path uses the same split for the levels above its subproblem size.
 struct BandPlan {
   int nb;
   int logL[3];
   int R[3];
 };
 
-__device__ __forceinline__ BandPlan band_plan(int logN) {
+__host__ __device__ __forceinline__ BandPlan band_plan(int logN, int log_bottom = LOG_LEAF) {
   BandPlan b;
-  int nl = logN - 2 - LOG_LEAF;
+  int nl = logN - 2 - log_bottom;
   int top = logN - 2;
   b.nb = 0;
   while (nl > 0 && b.nb < 3) {

@@ -299,6 +299,118 @@ __device__ __forceinline__ void store16(unsigned* __restrict__ out, long long of
 }
 
 // ---------------------------------------------------------------------
+// chain of the time-first variants, cluster path: two levels per pass
+// ---------------------------------------------------------------------
+// Levels M and 2M of the D_n frequency phase (dct S(k) = E(k) + O(k),
+// S(M/2-k) = E(k) - O(k); dst S(k) = O(k-1) + E(k), S(M/2-k) = O(k-1) - E(k))
+// in one read / barrier / write pass: item j takes E_M(j) and O_M(j), forms
+// S_M(j) and S_M(M/2-j), and combines each with the 2M tree's O_2M at the same
+// harmonic, giving S_2M at j, M-j, M/2-j and M/2+j.  The float32 operations
+// and their order are those of two separate levels.  FINAL (2M = N): the
+// result is written in natural order, unswizzled, word k holding harmonic k
+// (DST words 0 and N/2 zero), the layout the cluster store reads.
+template <int V, int TPB, int LOGM, bool FINAL>
+__device__ __forceinline__ void pass_chain2(float* R, int half, int ctx) {
+  constexpr int M = 1 << LOGM, Q1 = M / 4, Q2 = M / 2, L1 = LOGM - 2, L2 = LOGM - 1;
+  constexpr int NI = (Q1 + 1 + TPB - 1) / TPB;
+  const int P1 = half - M / 2, P2 = half - M;
+  float va[NI], vb[NI], vc[NI], vd[NI];
+#pragma unroll
+  for (int s = 0; s < NI; ++s) {
+    const int w = (int)threadIdx.x + s * TPB;
+    va[s] = vb[s] = vc[s] = vd[s] = 0.f;
+    if (ctx == 0 && w <= Q1) {
+      const int j = w;
+      float sA, sB = 0.f;
+      if (j < Q1) {
+        const float e = R[sw(P1 + Q1 + j)], o = R[sw(P1 + brev(j, L1))];
+        sA = e + o;
+        sB = e - o;
+      } else {
+        sA = R[sw(P1 + 2 * Q1)];
+      }
+      const float o2 = R[sw(P2 + brev(j, L2))];
+      va[s] = sA + o2;
+      vb[s] = sA - o2;
+      if (j < Q1) {
+        if (j > 0) {
+          const float o2b = R[sw(P2 + brev(Q2 - j, L2))];
+          vc[s] = sB + o2b;
+          vd[s] = sB - o2b;
+        } else {
+          vc[s] = sB;  // S_2M(M/2) = S_M(M/2)
+        }
+      }
+    } else if (ctx == 1 && w < Q1) {
+      const int j = w + 1;
+      float sA, sB = 0.f;
+      if (j < Q1) {
+        const float o = R[sw(P1 + brev(j - 1, L1))], e = R[sw(P1 + Q1 + j - 1)];
+        sA = o + e;
+        sB = o - e;
+      } else {
+        sA = R[sw(P1 + Q1 - 1)];  // S_M(M/4) = O_M(M/4 - 1)
+      }
+      const float o2 = R[sw(P2 + brev(j - 1, L2))];
+      va[s] = o2 + sA;
+      vb[s] = o2 - sA;
+      if (j < Q1) {
+        const float o2b = R[sw(P2 + brev(Q2 - j - 1, L2))];
+        vc[s] = o2b + sB;
+        vd[s] = o2b - sB;
+      }
+    }
+  }
+  float mid = 0.f;
+  if (FINAL && ctx == 1 && threadIdx.x == 0) mid = R[sw(P2 + Q2 - 1)];  // S_N(N/4) = O_N(N/4 - 1)
+  __syncthreads();
+  auto put = [&](int k, float v) {
+    if constexpr (FINAL) R[k] = v;
+    else R[sw(P2 + (ctx == 0 ? k : k - 1))] = v;
+  };
+#pragma unroll
+  for (int s = 0; s < NI; ++s) {
+    const int w = (int)threadIdx.x + s * TPB;
+    if (ctx == 0 && w <= Q1) {
+      const int j = w;
+      put(j, va[s]);
+      put(M - j, vb[s]);
+      if (j < Q1) {
+        if (j > 0) {
+          put(Q2 - j, vc[s]);
+          put(Q2 + j, vd[s]);
+        } else {
+          put(Q2, vc[s]);
+        }
+      }
+    } else if (ctx == 1 && w < Q1) {
+      const int j = w + 1;
+      put(j, va[s]);
+      put(M - j, vb[s]);
+      if (j < Q1) {
+        put(Q2 - j, vc[s]);
+        put(Q2 + j, vd[s]);
+      }
+    }
+  }
+  if (FINAL && ctx == 1 && threadIdx.x == 0) {
+    R[Q2] = mid;
+    R[0] = 0.f;
+    R[2 * Q2] = 0.f;
+  }
+}
+
+// Pairs of chain levels LO, LO + 1, ... below the final pair (LN - 1, LN).
+template <int V, int TPB, int LN, int LO>
+__device__ __forceinline__ void chain_pairs(float* R, int half, int ctx) {
+  if constexpr (LO + 1 <= LN - 2) {
+    pass_chain2<V, TPB, LO, false>(R, half, ctx);
+    __syncthreads();
+    chain_pairs<V, TPB, LN, LO + 2>(R, half, ctx);
+  }
+}
+
+// ---------------------------------------------------------------------
 // store of the cluster path, in two stages
 // ---------------------------------------------------------------------
 // Stage 1, local: the CTA's own region is rewritten in natural frequency
@@ -588,9 +700,23 @@ __device__ __forceinline__ void fused_body(const FusedArgs& a, const SmallConsts
         __syncthreads();
       }
     }
-    for (int lm = LOG_LEAF + 2; lm <= logN - 1; ++lm) {
-      pass_chain<V, TPB, MAXI>(sm, g, lm);
-      __syncthreads();
+    if constexpr (CL > 1 && LN > 0) {
+      // levels 2^7 .. 2^(LN-2) in pairs (a single level first when their
+      // count is odd), then the final pair (2^(LN-1), 2^LN) in natural order
+      constexpr int LO = LOG_LEAF + 2;
+      constexpr int LO2 = ((LN - 1 - LO) & 1) ? LO + 1 : LO;
+      const int ctx = (int)cg::this_cluster().block_rank() & 1;
+      if constexpr (LO2 > LO) {
+        pass_chain<V, TPB, MAXI>(sm, g, LO);
+        __syncthreads();
+      }
+      chain_pairs<V, TPB, LN, LO2>(sm, half, ctx);
+      pass_chain2<V, TPB, LN - 1, true>(sm, half, ctx);
+    } else {
+      for (int lm = LOG_LEAF + 2; lm <= logN - 1; ++lm) {
+        pass_chain<V, TPB, MAXI>(sm, g, lm);
+        __syncthreads();
+      }
     }
   } else {
     for (int lm = logN - 1; lm >= LOG_LEAF + 2; --lm) {
@@ -624,8 +750,11 @@ __device__ __forceinline__ void fused_body(const FusedArgs& a, const SmallConsts
 
   // ---- store ----
   if constexpr (CL > 1 && LN > 0) {
-    __syncthreads();
-    region_to_natural<V, TPB, LN>(sm, (int)cg::this_cluster().block_rank() & 1);
+    // time-first variants: the final chain pair already wrote natural order
+    if constexpr (!Var<V>::ot) {
+      __syncthreads();
+      region_to_natural<V, TPB, LN>(sm, (int)cg::this_cluster().block_rank() & 1);
+    }
     cg::this_cluster().sync();
     const long long t = tid(0);
     store_natural_cluster<TPB, LN>(sm, a, t, toff(t), cj, tot);

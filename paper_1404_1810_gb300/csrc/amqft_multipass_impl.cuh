@@ -4,10 +4,10 @@
 //
 //   load     D_c, D_r (and the first D_k for the harmonics-first variants),
 //            scattered into the regions;
-//   levels   tree levels of node size > S and chain levels of periodisation
-//            > 4S, one kernel per level: in-place quartets for the D_k time
-//            phase (ot trees) and the D_n frequency phase (to trees), gather
-//            form with a second workspace for the others;
+//   levels   tree levels of node size > S in bands of up to four levels per
+//            pass (the fused kernel's fold and chunk bands, in place in the
+//            workspace), the M2/M6 time phase one level per pass in gather
+//            form, and chain levels of periodisation > 4S one per pass;
 //   solve    one CTA per pair of tree nodes of size S (node mode) and one per
 //            region tail (the trees of size <= S plus the chain up to 4S, a
 //            region of N' = 4S) in shared memory, with the fused kernel's
@@ -133,23 +133,27 @@ __global__ void mp_store16_kernel(MpArgs a, const float* W, const int* Mx) {
   }
 }
 
-// in-place quartet level over every region (fwd: ot D_k time phase; else to
-// D_n frequency phase) at node size 2^logLp
-template <int V, bool FWD>
-__global__ void mp_quartet_kernel(MpArgs a, float* W, int logLp) {
-  const int half = 1 << (a.logN - 1), logQ = logLp - 2;
-  const long long nb = (half >> logLp) - 1;
-  const long long per = nb << logQ;
-  const long long total = per * 4 * mp_nt(a);
-  for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
-    const long long rr = w / per, rem = w - rr * per;
-    float* R = W + rr * a.RSg;
-    const int ctx0 = (int)(rr & 1);
-    const int p0 = (int)(rem >> logQ) << logLp, i = (int)(rem & ((1 << logQ) - 1));
-    const int ctx = node_ctx<V>(p0, logLp, half, ctx0);
-    if constexpr (FWD) fwd_ot_quartet<V>(R, p0, logLp, ctx, i, a.ctab);
-    else bwd_to_quartet<V>(R, p0, logLp, ctx, i, a.ctab);
-  }
+// Region geometry of the workspace for the band kernels (every region of
+// the chunk, in global memory).
+__device__ __forceinline__ Geo mp_geo(const MpArgs& a) {
+  Geo g;
+  g.logN = a.logN;
+  g.half = 1 << (a.logN - 1);
+  g.RS = (int)a.RSg;
+  g.nreg = (int)(4 * mp_nt(a));
+  g.nreg_cap = g.nreg;
+  g.gbase = 0;
+  g.sub = 0;
+  return g;
+}
+
+// Up to four tree levels above the subproblem size in one pass over the
+// workspace: the fused kernel's fold band (D_k + M_v time phase of the ot
+// trees, or D_n + M_v frequency phase of the to trees), in place.
+template <int V, bool FWD, int R>
+__global__ void __launch_bounds__(256) mp_fold_band_kernel(MpArgs a, float* W, int logL) {
+  const Geo g = mp_geo(a);
+  run_fold_band<V, FWD, R, 256, true>(W, g, logL, a.ctab);
 }
 
 // Neighbour form of M_v on the B halves at node size 2^logLp (M4/M8
@@ -400,13 +404,29 @@ cudaError_t mp_run(const MpArgs& a0, float* W0, float* W1, const SmallConsts& K,
   if (e != cudaSuccess) return e;
   const int half = N / 2;
   const unsigned nsolve = (unsigned)(4 * a.nt * ((half >> MP_LOG_S) / 2));  // nnode/2 + 1 per region
-  if constexpr (Var<V>::ot) {
-    for (int lp = logN - 2; lp >= MP_LOG_S + 1; --lp) {
-      mp_quartet_kernel<V, true><<<grid_for(4 * a.nt * (half >> 2)), threads, 0, st>>>(a, cur, lp);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  // levels above the subproblem size, in bands of up to four levels
+  const BandPlan bp = band_plan(logN, MP_LOG_S);
+  auto fold = [&](int b, bool fwd) -> cudaError_t {
+    const unsigned grid = grid_for(4 * a.nt * (half >> 2));
+    switch (bp.R[b] * 2 + (fwd ? 1 : 0)) {
+      case 3: mp_fold_band_kernel<V, true, 1><<<grid, threads, 0, st>>>(a, cur, bp.logL[b]); break;
+      case 2: mp_fold_band_kernel<V, false, 1><<<grid, threads, 0, st>>>(a, cur, bp.logL[b]); break;
+      case 5: mp_fold_band_kernel<V, true, 2><<<grid, threads, 0, st>>>(a, cur, bp.logL[b]); break;
+      case 4: mp_fold_band_kernel<V, false, 2><<<grid, threads, 0, st>>>(a, cur, bp.logL[b]); break;
+      case 7: mp_fold_band_kernel<V, true, 3><<<grid, threads, 0, st>>>(a, cur, bp.logL[b]); break;
+      case 6: mp_fold_band_kernel<V, false, 3><<<grid, threads, 0, st>>>(a, cur, bp.logL[b]); break;
+      case 9: mp_fold_band_kernel<V, true, 4><<<grid, threads, 0, st>>>(a, cur, bp.logL[b]); break;
+      default: mp_fold_band_kernel<V, false, 4><<<grid, threads, 0, st>>>(a, cur, bp.logL[b]); break;
     }
+    return cudaGetLastError();
+  };
+  if constexpr (Var<V>::ot) {
+    for (int b = 0; b < bp.nb; ++b)
+      if ((e = fold(b, true)) != cudaSuccess) return e;
     mp_solve_kernel<V, MP_TPB><<<nsolve, MP_TPB, smem, st>>>(a, cur, K);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    // frequency phase of M4 / M8, one level per pass in gather form (a band
+    // would read its descendants bit-reversed, scattered across sectors)
     for (int lp = MP_LOG_S + 1; lp <= logN - 2; ++lp) {
       mp_neighbour_kernel<V><<<grid_for(words), threads, 0, st>>>(a, cur, oth, lp);
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -430,10 +450,8 @@ cudaError_t mp_run(const MpArgs& a0, float* W0, float* W1, const SmallConsts& K,
     }
     mp_solve_kernel<V, MP_TPB><<<nsolve, MP_TPB, smem, st>>>(a, cur, K);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    for (int lp = MP_LOG_S + 1; lp <= logN - 2; ++lp) {
-      mp_quartet_kernel<V, false><<<grid_for(4 * a.nt * (half >> 2)), threads, 0, st>>>(a, cur, lp);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
+    for (int b = bp.nb - 1; b >= 0; --b)
+      if ((e = fold(b, false)) != cudaSuccess) return e;
   }
   if (a.dtype == 0) {
     mp_store_kernel<V><<<grid_for(a.nt * (N / 4)), threads, 0, st>>>(a, cur);

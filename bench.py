@@ -7,10 +7,13 @@ synthetic), i.e. 2^29 transformed points per step.  Every buffer is 2 GiB,
 far larger than the 126 MB L2, so no L2 flush is needed between steps.
 
 Prints one JSON line (rank 0).  `value` is device time only (inputs resident
-in HBM); `e2e` adds the pinned host->device copy of the input and the
-device->host copy of the result every step; `roofline` is the forward kernel
-(16 bytes per point) against the measured HBM copy bandwidth; `cpu_baseline`
-is the CPU oracle (float64 recursion) on the host cores.
+in HBM); `e2e` is the batch's forward transform from pinned host memory to
+pinned host memory through the library's host-memory entry point (every step
+copies the whole input in and the whole result out, chunk by chunk, the
+copies overlapping the transforms); `roofline` is the forward kernel (16 bytes
+per point) against the measured HBM copy bandwidth; `cpu_baseline` is the CPU
+oracle (float64 recursion) on the host cores.  --workload c1|c3|c4|c5 prints
+the line of another configuration instead.
 
   python bench.py [--steps K] [--warmup W] [--variant V]
   python -m torch.distributed.run --nproc-per-node N bench.py --gpus N   (weak scaling)
@@ -510,6 +513,7 @@ def main():
 
     import synth
     from paper_1404_1810_gb300 import Plan, build, load
+    from paper_1404_1810_gb300.multi import max_over_ranks
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -560,10 +564,7 @@ def main():
     total_ms = ev[0][0].elapsed_time(ev[K - 1][2])
     fwd_ms = statistics.mean(ev[i][0].elapsed_time(ev[i][1]) for i in range(K))
     inv_ms = statistics.mean(ev[i][1].elapsed_time(ev[i][2]) for i in range(K))
-    t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms)
     ms_step = total_ms / K
     points_step = 2 * args.batch * n * world
     value = points_step / (ms_step * 1e-3) / 1e9
@@ -589,36 +590,31 @@ def main():
                     "bitexact_vs_f32_recursion": exact, "sample": "transforms 0 and batch-1"}
 
     if not args.no_e2e:
+        # through the host-memory entry point: the batch's forward transform
+        # from pinned host memory to pinned host memory, the copies of each
+        # chunk overlapping the transform of the next inside the call
         xh = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
-        zh = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
+        yh = torch.empty(x.shape, dtype=x.dtype, pin_memory=True)
         xh.copy_(x)
-        xd = torch.empty_like(x)
         ke = max(1, args.e2e_steps)
         for _ in range(2):
-            xd.copy_(xh, non_blocking=True)
-            plan.fwd(xd, y, stream)
-            plan.inv(y, z, stream)
-            zh.copy_(z, non_blocking=True)
+            plan.fwd_host(xh, yh, stream=stream)
         torch.cuda.synchronize()
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(ke):
-            xd.copy_(xh, non_blocking=True)
-            plan.fwd(xd, y, stream)
-            plan.inv(y, z, stream)
-            zh.copy_(z, non_blocking=True)
+            plan.fwd_host(xh, yh, stream=stream)
         e1.record(stream)
         torch.cuda.synchronize()
         barrier()
-        te = torch.tensor([e0.elapsed_time(e1) / ke], device=dev, dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        te = max_over_ranks(e0.elapsed_time(e1) / ke)
         nbytes = x.numel() * x.element_size()
-        e2e = {"value": points_step / (float(te.item()) * 1e-3) / 1e9, "unit": UNIT,
+        e2e = {"value": args.batch * n * world / (te * 1e-3) / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": nbytes, "d2h_bytes_per_step": nbytes,
-               "ms_per_step": float(te.item()), "steps": ke}
-        del xh, zh, xd
+               "ms_per_step": te, "steps": ke,
+               "step": "one forward transform of the batch, pinned host -> pinned host, through amqft_exec_host"}
+        del xh, yh
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(x[:256].cpu().numpy().astype(np.complex128), args.variant)

@@ -89,7 +89,25 @@ int amqft_exec_fwd(amqft_plan_t plan, const void *in, void *out, int32_t *exp_ou
 int amqft_exec_inv(amqft_plan_t plan, const void *in, const int32_t *exp_in, void *out,
                    int32_t *exp_out, void *stream);
 
-/* Release the plan and its device constant table.  NULL is accepted. */
+/* Transform the plan's batch from HOST memory to HOST memory: forward
+ * (direction 0) or unnormalised inverse (direction 1) of `batch` complex64
+ * transforms at in (read) and out (written), both host pointers, 8-byte
+ * aligned, not overlapping; page-locked memory lets the copies overlap the
+ * transforms (pageable memory works, with synchronous copies).  The batch runs
+ * in chunks of `chunk` transforms (0: about 64 MiB per chunk): each chunk is
+ * copied to the device, transformed by the same kernels as amqft_exec_fwd/inv
+ * and copied back, the copy-in of chunk i + 1 and the copy-out of chunk i - 1
+ * overlapping the transform of chunk i on three internal streams.  The call is
+ * asynchronous: `stream` is joined at the end, so out is complete once stream
+ * is.  The first call (or one with a larger chunk) allocates the plan's
+ * staging: two input and two output buffers of `chunk` transforms.  Calls on
+ * one plan must not run concurrently from several host threads.
+ * Errors: AMQFT_ERR_ARG (NULL or ragged plan, direction, chunk < 0),
+ * AMQFT_ERR_DTYPE (16-bit plans), AMQFT_ERR_ALIGN, AMQFT_ERR_INPLACE,
+ * AMQFT_ERR_NOMEM (staging), AMQFT_ERR_CUDA. */
+int amqft_exec_host(amqft_plan_t plan, const void *in, void *out, int direction, int64_t chunk, void *stream);
+
+/* Release the plan and everything it owns.  NULL is accepted. */
 int amqft_destroy(amqft_plan_t plan);
 
 /* Message of the last error on the calling thread ("" if none).  The string

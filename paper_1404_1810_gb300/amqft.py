@@ -59,6 +59,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.amqft_ragged_tune.restype = i32
         lib.amqft_ragged_skipped.argtypes = [vp, ctypes.POINTER(i64)]
         lib.amqft_ragged_skipped.restype = i32
+        lib.amqft_exec_host.argtypes = [vp, vp, vp, i32, i64, vp]
+        lib.amqft_exec_host.restype = i32
         lib.amqft_exec_static.argtypes = [vp, i64, vp, vp, i32, vp]
         lib.amqft_exec_static.restype = i32
         lib.amqft_plan_info.argtypes = [vp] + [ctypes.POINTER(i32)] * 4
@@ -94,6 +96,10 @@ def amqft_exec_static(plan: int, batch: int, d_in: int, d_out: int, inverse: int
     no allocation in the call; calls overlapping in time on one device race."""
     _check(load().amqft_exec_static(plan, int(batch), d_in, d_out, int(inverse), stream or None),
            "amqft_exec_static")
+
+
+def amqft_exec_host(plan: int, h_in: int, h_out: int, direction: int = 0, chunk: int = 0, stream: int = 0) -> None:
+    _check(load().amqft_exec_host(plan, h_in, h_out, int(direction), int(chunk), stream or None), "amqft_exec_host")
 
 
 def amqft_plan_ragged(max_log2n: int, variant: int, dtype: int, max_count: int, max_points: int) -> int:
@@ -224,6 +230,28 @@ class Plan:
         amqft_exec_inv(self.handle, x.data_ptr(), exp_in.data_ptr() if exp_in is not None else 0, out.data_ptr(),
                        exp_out.data_ptr(), _stream_handle(stream))
         return out, exp_out
+
+    def _host(self, x, out, inverse, chunk, stream):
+        import torch
+
+        for t, name in ((x, "x"), (out, "out")):
+            if t is not None and (t.dtype != torch.complex64 or t.is_cuda or not t.is_contiguous()):
+                raise ValueError(f"{name} must be a contiguous complex64 CPU tensor (pinned for overlap)")
+        if x.numel() != self.batch * self.n:
+            raise ValueError(f"x has {x.numel()} elements, plan needs {self.batch * self.n}")
+        if out is None:
+            out = torch.empty_like(x, pin_memory=x.is_pinned())
+        amqft_exec_host(self.handle, x.data_ptr(), out.data_ptr(), 1 if inverse else 0, chunk,
+                        _stream_handle(stream))
+        return out
+
+    def fwd_host(self, x, out=None, chunk: int = 0, stream=None):
+        """DFT of a host batch into host memory (complete once `stream` is)."""
+        return self._host(x, out, False, chunk, stream)
+
+    def inv_host(self, x, out=None, chunk: int = 0, stream=None):
+        """Unnormalised inverse of a host batch into host memory."""
+        return self._host(x, out, True, chunk, stream)
 
     def close(self):
         if getattr(self, "handle", 0):

@@ -205,6 +205,12 @@ struct amqft_plan_s {
   int* d_rlist;    // (log2n + 1) lists of max_count transform ids
   float* d_rwork;  // multi-pass workspace, shared by the lengths above 2^16 in turn
   int knob[4];     // schedule, order, small CTAs per SM, cluster grid multiplier
+  // host-memory execution (amqft_exec_host): two in and two out staging
+  // buffers of h_chunk transforms, copy-in / transform / copy-out streams
+  long long h_chunk;
+  void* h_buf[4];
+  cudaStream_t h_st[3];
+  cudaEvent_t h_ev[8];
 };
 
 // workspace budget of one plan (both ping-pong buffers)
@@ -290,6 +296,10 @@ int amqft_plan(amqft_plan_t* out, int log2n, int variant, int64_t batch, int dty
   p->knob[1] = 0;
   p->knob[2] = 1;
   p->knob[3] = 1;
+  p->h_chunk = 0;
+  memset(p->h_buf, 0, sizeof p->h_buf);
+  memset(p->h_st, 0, sizeof p->h_st);
+  memset(p->h_ev, 0, sizeof p->h_ev);
   // level-major table: periodisation M = 16..N holds M/8 constants at [M/8-2, M/4-2)
   const long long N = 1LL << log2n;
   const long long ntab = N >= 16 ? N / 4 - 2 : 0;
@@ -328,13 +338,12 @@ int amqft_plan(amqft_plan_t* out, int log2n, int variant, int64_t batch, int dty
   return AMQFT_OK;
 }
 
-static int exec(amqft_plan_t p, const void* in, void* out, int inverse, const int32_t* exp_in, int32_t* exp_out,
-                void* stream) {
-  t_err.clear();
-  if (!p) return fail(AMQFT_ERR_ARG, "plan is NULL");
+// `batch` transforms (at most the plan's batch) from in to out on stream.
+static int exec_n(amqft_plan_t p, long long batch, const void* in, void* out, int inverse, const int32_t* exp_in,
+                  int32_t* exp_out, void* stream) {
   const bool c64 = p->dtype == AMQFT_C64;
   if (c64 && (exp_in || exp_out)) return fail(AMQFT_ERR_DTYPE, "exponent arrays are only used with 16-bit storage");
-  if (p->batch == 0) return AMQFT_OK;
+  if (batch == 0) return AMQFT_OK;
   if (!in || !out) return fail(AMQFT_ERR_ALIGN, "in or out is NULL");
   const uintptr_t amask = c64 ? 7u : 3u;
   if (((uintptr_t)in | (uintptr_t)out) & amask)
@@ -344,14 +353,14 @@ static int exec(amqft_plan_t p, const void* in, void* out, int inverse, const in
     if (((uintptr_t)exp_out | (uintptr_t)exp_in) & 3u) return fail(AMQFT_ERR_ALIGN, "exponent arrays must be 4-byte aligned");
   }
   const long long N = 1LL << p->log2n;
-  const uintptr_t bytes = (uintptr_t)(N * p->batch * (c64 ? 8 : 4));
+  const uintptr_t bytes = (uintptr_t)(N * batch * (c64 ? 8 : 4));
   const uintptr_t a0 = (uintptr_t)in, b0 = (uintptr_t)out;
   if (a0 < b0 + bytes && b0 < a0 + bytes) return fail(AMQFT_ERR_INPLACE, "in and out overlap");
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;
   if (p->log2n > AMQFT_LOG2N_FUSED_MAX) {
     const long long per_buf = p->chunk * 4 * p->RSg;
-    for (long long t0 = 0; t0 < p->batch; t0 += p->chunk) {
+    for (long long t0 = 0; t0 < batch; t0 += p->chunk) {
       MpArgs a;
       a.in = in;
       a.out = out;
@@ -359,7 +368,7 @@ static int exec(amqft_plan_t p, const void* in, void* out, int inverse, const in
       a.exp_out = exp_out;
       a.dtype = p->dtype;
       a.ctab = p->d_ctab;
-      a.nt = (p->batch - t0) < p->chunk ? (p->batch - t0) : p->chunk;
+      a.nt = (batch - t0) < p->chunk ? (batch - t0) : p->chunk;
       a.t0 = t0;
       a.logN = p->log2n;
       a.inverse = inverse;
@@ -373,9 +382,9 @@ static int exec(amqft_plan_t p, const void* in, void* out, int inverse, const in
     return AMQFT_OK;
   }
   if (p->log2n == 0) {
-    const unsigned grid = (unsigned)((p->batch + 255) / 256);
-    if (c64) copy1_kernel<<<grid, 256, 0, st>>>((const float2*)in, (float2*)out, p->batch);
-    else copy1_16_kernel<<<grid, 256, 0, st>>>((const unsigned*)in, (unsigned*)out, exp_in, exp_out, p->batch,
+    const unsigned grid = (unsigned)((batch + 255) / 256);
+    if (c64) copy1_kernel<<<grid, 256, 0, st>>>((const float2*)in, (float2*)out, batch);
+    else copy1_16_kernel<<<grid, 256, 0, st>>>((const unsigned*)in, (unsigned*)out, exp_in, exp_out, batch,
                                                p->dtype);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "copy kernel launch");
@@ -388,7 +397,7 @@ static int exec(amqft_plan_t p, const void* in, void* out, int inverse, const in
   a.exp_out = exp_out;
   a.dtype = p->dtype;
   a.ctab = p->d_ctab;
-  a.batch = p->batch;
+  a.batch = batch;
   a.logN = p->log2n;
   a.tpc = p->cfg.per_cta;
   a.inverse = inverse;
@@ -402,12 +411,96 @@ static int exec(amqft_plan_t p, const void* in, void* out, int inverse, const in
 }
 
 int amqft_exec_fwd(amqft_plan_t p, const void* in, void* out, int32_t* exp_out, void* stream) {
-  return exec(p, in, out, 0, nullptr, exp_out, stream);
+  t_err.clear();
+  if (!p) return fail(AMQFT_ERR_ARG, "plan is NULL");
+  return exec_n(p, p->batch, in, out, 0, nullptr, exp_out, stream);
 }
 
 int amqft_exec_inv(amqft_plan_t p, const void* in, const int32_t* exp_in, void* out, int32_t* exp_out,
                    void* stream) {
-  return exec(p, in, out, 1, exp_in, exp_out, stream);
+  t_err.clear();
+  if (!p) return fail(AMQFT_ERR_ARG, "plan is NULL");
+  return exec_n(p, p->batch, in, out, 1, exp_in, exp_out, stream);
+}
+
+// Host-memory execution: staging on the device, three internal streams.
+static void host_release(amqft_plan_t p) {
+  for (int i = 0; i < 4; ++i)
+    if (p->h_buf[i]) cudaFree(p->h_buf[i]);
+  for (int i = 0; i < 3; ++i)
+    if (p->h_st[i]) cudaStreamDestroy(p->h_st[i]);
+  for (int i = 0; i < 8; ++i)
+    if (p->h_ev[i]) cudaEventDestroy(p->h_ev[i]);
+  memset(p->h_buf, 0, sizeof p->h_buf);
+  memset(p->h_st, 0, sizeof p->h_st);
+  memset(p->h_ev, 0, sizeof p->h_ev);
+  p->h_chunk = 0;
+}
+
+int amqft_exec_host(amqft_plan_t p, const void* in, void* out, int direction, int64_t chunk, void* stream) {
+  t_err.clear();
+  if (!p) return fail(AMQFT_ERR_ARG, "plan is NULL");
+  if (p->ragged) return fail(AMQFT_ERR_ARG, "amqft_exec_host: not for ragged plans");
+  if (p->dtype != AMQFT_C64) return fail(AMQFT_ERR_DTYPE, "amqft_exec_host: AMQFT_C64 plans only");
+  if (direction != 0 && direction != 1) return fail(AMQFT_ERR_ARG, "amqft_exec_host: direction must be 0 or 1");
+  if (chunk < 0) return fail(AMQFT_ERR_ARG, "amqft_exec_host: chunk=%lld < 0", (long long)chunk);
+  if (p->batch == 0) return AMQFT_OK;
+  if (!in || !out) return fail(AMQFT_ERR_ALIGN, "amqft_exec_host: in or out is NULL");
+  if (((uintptr_t)in | (uintptr_t)out) & 7u) return fail(AMQFT_ERR_ALIGN, "amqft_exec_host: in/out must be 8-byte aligned");
+  const long long N = 1LL << p->log2n, tbytes = N * 8;
+  const uintptr_t bytes = (uintptr_t)(tbytes * p->batch), a0 = (uintptr_t)in, b0 = (uintptr_t)out;
+  if (a0 < b0 + bytes && b0 < a0 + bytes) return fail(AMQFT_ERR_INPLACE, "amqft_exec_host: in and out overlap");
+  long long C = chunk > 0 ? chunk : (64LL << 20) / tbytes;
+  if (C < 1) C = 1;
+  if (C > p->batch) C = p->batch;
+  cudaError_t e = cudaSuccess;
+  if (p->h_chunk < C) {  // first use, or a larger chunk: (re)allocate the staging
+    host_release(p);
+    for (int i = 0; i < 4 && e == cudaSuccess; ++i) e = cudaMalloc(&p->h_buf[i], (size_t)(C * tbytes));
+    for (int i = 0; i < 3 && e == cudaSuccess; ++i) e = cudaStreamCreateWithFlags(&p->h_st[i], cudaStreamNonBlocking);
+    for (int i = 0; i < 8 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&p->h_ev[i], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      host_release(p);
+      return fail(AMQFT_ERR_NOMEM, "amqft_exec_host: staging allocation failed: %s", cudaGetErrorString(e));
+    }
+    p->h_chunk = C;
+  }
+  cudaStream_t caller = (cudaStream_t)stream, s_in = p->h_st[0], s_comp = p->h_st[1], s_out = p->h_st[2];
+  cudaEvent_t* ev_in = p->h_ev;        // [0, 2): copy-in of slot s done
+  cudaEvent_t* ev_comp = p->h_ev + 2;  // [2, 4): transform of slot s done
+  cudaEvent_t* ev_out = p->h_ev + 4;   // [4, 6): copy-out of slot s done
+  cudaEvent_t ev_start = p->h_ev[6], ev_join = p->h_ev[7];
+  if ((e = cudaEventRecord(ev_start, caller)) != cudaSuccess) return cuda_fail(e, "amqft_exec_host: cudaEventRecord");
+  for (int i = 0; i < 3; ++i) cudaStreamWaitEvent(p->h_st[i], ev_start, 0);
+  const char* hin = static_cast<const char*>(in);
+  char* hout = static_cast<char*>(out);
+  int slot = 0;
+  for (long long t0 = 0; t0 < p->batch; t0 += C, slot ^= 1) {
+    const long long c = (p->batch - t0) < C ? (p->batch - t0) : C;
+    void* din = p->h_buf[slot];
+    void* dout = p->h_buf[2 + slot];
+    // copy in once the transform that last read this slot is done
+    cudaStreamWaitEvent(s_in, ev_comp[slot], 0);
+    e = cudaMemcpyAsync(din, hin + t0 * tbytes, (size_t)(c * tbytes), cudaMemcpyHostToDevice, s_in);
+    if (e != cudaSuccess) return cuda_fail(e, "amqft_exec_host: copy in");
+    cudaEventRecord(ev_in[slot], s_in);
+    // transform once the copy in is done and the last copy out of this slot is done
+    cudaStreamWaitEvent(s_comp, ev_in[slot], 0);
+    cudaStreamWaitEvent(s_comp, ev_out[slot], 0);
+    const int rc = exec_n(p, c, din, dout, direction, nullptr, nullptr, s_comp);
+    if (rc != AMQFT_OK) return rc;
+    cudaEventRecord(ev_comp[slot], s_comp);
+    // copy out
+    cudaStreamWaitEvent(s_out, ev_comp[slot], 0);
+    e = cudaMemcpyAsync(hout + t0 * tbytes, dout, (size_t)(c * tbytes), cudaMemcpyDeviceToHost, s_out);
+    if (e != cudaSuccess) return cuda_fail(e, "amqft_exec_host: copy out");
+    cudaEventRecord(ev_out[slot], s_out);
+  }
+  // the last copy out follows every earlier operation of the call
+  cudaEventRecord(ev_join, s_out);
+  e = cudaStreamWaitEvent(caller, ev_join, 0);
+  if (e != cudaSuccess) return cuda_fail(e, "amqft_exec_host: join");
+  return AMQFT_OK;
 }
 
 int amqft_destroy(amqft_plan_t p) {
@@ -418,6 +511,7 @@ int amqft_destroy(amqft_plan_t p) {
   if (p->d_rcnt) cudaFree(p->d_rcnt);
   if (p->d_rlist) cudaFree(p->d_rlist);
   if (p->d_rwork) cudaFree(p->d_rwork);
+  host_release(p);
   delete p;
   return AMQFT_OK;
 }

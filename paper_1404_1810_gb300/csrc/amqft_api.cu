@@ -23,18 +23,20 @@ FusedConfig fused_config(int logN) {
   c.RS = region_stride(logN);
   if (logN <= 13) {
     c.cluster = 1;
-    c.threads = 512;
-    // a CTA holds 16384 region values: 512 threads x 32 values
+    c.threads = SMALL_TPB;
+    // a CTA holds 16384 region values: 256 threads x 64 values, two CTAs per SM
     c.per_cta = small_tpc(logN);
     c.nreg = 4 * c.per_cta;
   } else {
     c.cluster = 4;
     c.per_cta = 1;
     c.nreg = 1;
-    c.threads = half / 32;  // 32 region values per thread
+    // 2^14, 2^15: 256 threads (two CTAs per SM); 2^16: 1024 threads, 32 values each
+    c.threads = cluster_tpb(logN);
   }
   c.tot_off = ((c.nreg * c.RS + 31) / 32) * 32;
-  c.smem = (c.tot_off + c.threads + 32 + snap_floats(c.nreg * half)) * (int)sizeof(float);
+  // scan scratch (threads + 32), snapshot, and one 16-bit exponent slot per transform
+  c.smem = (c.tot_off + c.threads + 32 + snap_floats(c.nreg * half) + c.per_cta) * (int)sizeof(float);
   return c;
 }
 
@@ -294,7 +296,7 @@ int amqft_plan(amqft_plan_t* out, int log2n, int variant, int64_t batch, int dty
   p->d_rwork = nullptr;
   p->knob[0] = 1;
   p->knob[1] = 0;
-  p->knob[2] = 1;
+  p->knob[2] = 2;
   p->knob[3] = 1;
   p->h_chunk = 0;
   memset(p->h_buf, 0, sizeof p->h_buf);
@@ -600,7 +602,7 @@ int amqft_exec_ragged(amqft_plan_t p, int64_t count, const int64_t* d_offsets, c
   for (int c = 1; c <= 13 && c <= r.maxlog; ++c) {
     const int tpc = small_tpc(c);
     const int sm_bytes =
-        (small_tot_off(c) + 512 + 32 + snap_floats(4 * tpc * (1 << (c - 1)))) * (int)sizeof(float);
+        (small_tot_off(c) + SMALL_TPB + 32 + snap_floats(4 * tpc * (1 << (c - 1))) + tpc) * (int)sizeof(float);
     if (sm_bytes > L.small_smem) L.small_smem = sm_bytes;
   }
   for (int q = 0; q < 3; ++q) {

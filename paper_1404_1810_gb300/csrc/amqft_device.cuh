@@ -118,6 +118,19 @@ __host__ __device__ constexpr int region_stride(int logN) {
   return logN >= 7 ? (((1 << (logN - 1)) + 2 + 31) / 32) * 32 : (((logN >= 1 ? (1 << (logN - 1)) : 0) + 3) / 2) * 2;
 }
 
+// Launch shapes of the fused kernel, shared by every launch site and by the
+// host's shared-memory sizing.  N <= 2^13: one CTA of SMALL_TPB threads holds
+// 16384 region values (two CTAs per SM); 2^14..2^16: clusters of four CTAs,
+// one region each.  MAXI bounds the items a thread takes in the per-level
+// passes (MAXI * TPB must cover half a region).
+constexpr int SMALL_TPB = 256, SMALL_MAXI = 32;
+__host__ __device__ constexpr int cluster_tpb(int logN) { return logN == 16 ? 1024 : 256; }
+__host__ __device__ constexpr int cluster_maxi(int logN) { return logN == 15 ? 32 : 16; }
+static_assert(SMALL_TPB * SMALL_MAXI >= 8192, "per-level passes of the single-CTA path");
+static_assert(cluster_tpb(14) * cluster_maxi(14) >= (1 << 12) && cluster_tpb(15) * cluster_maxi(15) >= (1 << 13) &&
+                  cluster_tpb(16) * cluster_maxi(16) >= (1 << 14),
+              "per-level passes of the cluster path");
+
 // Context (0 DCT, 1 DST) of the tree node of size 2^logLp at region position p0.
 template <int V>
 __device__ __forceinline__ int node_ctx(int p0, int logLp, int half, int ctx0) {

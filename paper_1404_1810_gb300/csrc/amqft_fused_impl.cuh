@@ -632,24 +632,29 @@ __device__ __forceinline__ void fused_body(const FusedArgs& a, const SmallConsts
   float* snap = wsum + 32;
 
   // ---- load ----
-  // every configuration gives each thread exactly NIT orbit items
-  constexpr int NIT = (CL > 1 && LN > 0) ? (1 << (LN - 4)) / TPB : 4;
-  {
-    int n_[NIT], tau_[NIT];
-    bool ok_[NIT];
-    Fetched f_[NIT];
+  // every configuration gives each thread exactly NIT orbit items, taken in
+  // rounds of U so that a round's global loads are in flight together
+  constexpr int NIT = (CL > 1 && LN > 0) ? (1 << (LN - 4)) / TPB : 2048 / TPB;
+  constexpr int U = NIT < 4 ? NIT : 4, NR = NIT / U;
+  static_assert(NR * U == NIT, "orbit items per thread");
+#pragma unroll 1
+  for (int rd = 0; rd < NR; ++rd) {
+    int n_[U], tau_[U];
+    bool ok_[U];
+    Fetched f_[U];
 #pragma unroll
-    for (int s = 0; s < NIT; ++s) {
+    for (int s = 0; s < U; ++s) {
+      const int idx = rd * U + s;
       if constexpr (CL == 1) {
-        const int w = threadIdx.x + s * TPB;
+        const int w = threadIdx.x + idx * TPB;
         tau_[s] = w >> logQi;
         n_[s] = w & (Qi - 1);
         ok_[s] = tau_[s] < ntr;
       } else {
         const int per = Qi / CL;
         tau_[s] = 0;
-        n_[s] = (int)cg::this_cluster().block_rank() * per + threadIdx.x + s * TPB;
-        ok_[s] = (int)threadIdx.x + s * TPB < per;
+        n_[s] = (int)cg::this_cluster().block_rank() * per + threadIdx.x + idx * TPB;
+        ok_[s] = (int)threadIdx.x + idx * TPB < per;
       }
       if (ok_[s]) {
         const long long t = tid(tau_[s]);
@@ -657,7 +662,7 @@ __device__ __forceinline__ void fused_body(const FusedArgs& a, const SmallConsts
       }
     }
 #pragma unroll
-    for (int s = 0; s < NIT; ++s)
+    for (int s = 0; s < U; ++s)
       if (ok_[s]) load_scatter<V>(rg, logN, tau_[s], n_[s], f_[s]);
   }
   if constexpr (CL == 1) __syncthreads();
@@ -763,49 +768,64 @@ __device__ __forceinline__ void fused_body(const FusedArgs& a, const SmallConsts
   }
   if constexpr (CL > 1) cg::this_cluster().sync();
   {
-    int k_[4], tau_[4];
-    bool ok_[4];
-    Gathered g_[4];
-#pragma unroll
-    for (int s = 0; s < 4; ++s) {
+    static_assert(CL == 1 || LN > 0, "the cluster path stores through store_natural_cluster");
+    // item idx of this thread: (local transform, harmonic k)
+    auto item = [&](int idx, int& tau, int& k) -> bool {
       if constexpr (CL == 1) {
-        const int w = threadIdx.x + s * TPB;
-        tau_[s] = w >> logQi;
-        k_[s] = w & (Qi - 1);
-        ok_[s] = tau_[s] < ntr;
+        const int w = threadIdx.x + idx * TPB;
+        tau = w >> logQi;
+        k = w & (Qi - 1);
+        return tau < ntr;
       } else {
         const int per = Qi / CL;
-        tau_[s] = 0;
-        k_[s] = (int)cg::this_cluster().block_rank() * per + threadIdx.x + s * TPB;
-        ok_[s] = (int)threadIdx.x + s * TPB < per;
+        tau = 0;
+        k = (int)cg::this_cluster().block_rank() * per + threadIdx.x + idx * TPB;
+        return (int)threadIdx.x + idx * TPB < per;
       }
-      if (ok_[s]) g_[s] = store_gather<V>(rg, logN, tau_[s], k_[s]);
-    }
-    if (a.dtype == DT_C64) {
-#pragma unroll
-      for (int s = 0; s < 4; ++s)
-        if (ok_[s]) store_emit<V>(static_cast<float2*>(a.out), logN, toff(tid(tau_[s])), k_[s], g_[s], cj);
-    } else {
-      // 16-bit: one exponent per transform from its largest component
-      static_assert(CL == 1 || LN > 0, "the cluster path stores through store_natural_cluster");
-      Out4 o_[4];
-#pragma unroll
-      for (int s = 0; s < 4; ++s)
-        if (ok_[s]) o_[s] = emit_values<V>(logN, k_[s], g_[s]);
-      __syncthreads();  // every gather is done: region memory is free
-      int* slot = reinterpret_cast<int*>(sm);
+    };
+    // 16-bit: one exponent per transform from its largest component; the
+    // maxima go to their own slots after the scan scratch
+    int* slot = reinterpret_cast<int*>(snap + snap_floats(g.nreg_cap * half));
+    const bool c64 = a.dtype == DT_C64;
+    if (!c64) {
       for (int i = threadIdx.x; i < ntr; i += TPB) slot[i] = 0;
       __syncthreads();
+#pragma unroll 1
+      for (int rd = 0; rd < NR; ++rd) {
+        int k_[U], tau_[U];
+        bool ok_[U];
+        Gathered g_[U];
 #pragma unroll
-      for (int s = 0; s < 4; ++s)
-        if (ok_[s]) atomicMax(slot + tau_[s], __float_as_int(out4_absmax(o_[s])));
+        for (int s = 0; s < U; ++s) {
+          ok_[s] = item(rd * U + s, tau_[s], k_[s]);
+          if (ok_[s]) g_[s] = store_gather<V>(rg, logN, tau_[s], k_[s]);
+        }
+#pragma unroll
+        for (int s = 0; s < U; ++s)
+          if (ok_[s]) atomicMax(slot + tau_[s], __float_as_int(out4_absmax(emit_values<V>(logN, k_[s], g_[s]))));
+      }
       __syncthreads();
+    }
+#pragma unroll 1
+    for (int rd = 0; rd < NR; ++rd) {
+      int k_[U], tau_[U];
+      bool ok_[U];
+      Gathered g_[U];
 #pragma unroll
-      for (int s = 0; s < 4; ++s) {
-        if (ok_[s]) {
+      for (int s = 0; s < U; ++s) {
+        ok_[s] = item(rd * U + s, tau_[s], k_[s]);
+        if (ok_[s]) g_[s] = store_gather<V>(rg, logN, tau_[s], k_[s]);
+      }
+#pragma unroll
+      for (int s = 0; s < U; ++s) {
+        if (!ok_[s]) continue;
+        const long long t = tid(tau_[s]);
+        if (c64) {
+          store_emit<V>(static_cast<float2*>(a.out), logN, toff(t), k_[s], g_[s], cj);
+        } else {
           const int e = block_exponent(__int_as_float(slot[tau_[s]]));
-          const long long t = tid(tau_[s]);
-          store16(static_cast<unsigned*>(a.out), toff(t), o_[s], pow2f(-e), cj, a.dtype);
+          store16(static_cast<unsigned*>(a.out), toff(t), emit_values<V>(logN, k_[s], g_[s]), pow2f(-e), cj,
+                  a.dtype);
           if (k_[s] == 0) a.exp_out[t] = e;
         }
       }
@@ -815,7 +835,8 @@ __device__ __forceinline__ void fused_body(const FusedArgs& a, const SmallConsts
 }
 
 template <int V, int TPB, int MAXI, int CL, int LN>
-__global__ void __launch_bounds__(TPB) fused_kernel(const FusedArgs a, const __grid_constant__ SmallConsts K) {
+__global__ void __launch_bounds__(TPB, TPB <= 256 ? 2 : 1) fused_kernel(const FusedArgs a,
+                                                                   const __grid_constant__ SmallConsts K) {
   extern __shared__ __align__(16) float sm[];
   if constexpr (CL == 1) {
     const long long j0 = (long long)blockIdx.x * a.tpc;
@@ -860,12 +881,12 @@ template <int V>
 cudaError_t launch_v(const FusedArgs& a, const SmallConsts& K, const FusedConfig& c, cudaStream_t st) {
   if (c.cluster == 1) {
     const long long grid = (a.batch + c.per_cta - 1) / c.per_cta;
-    return launch_cfg<V, 512, 16, 1, 0>(a, K, grid, c.smem, st);
+    return launch_cfg<V, SMALL_TPB, SMALL_MAXI, 1, 0>(a, K, grid, c.smem, st);
   }
   switch (a.logN) {
-    case 14: return launch_cfg<V, 256, 16, 4, 14>(a, K, a.batch, c.smem, st);
-    case 15: return launch_cfg<V, 512, 16, 4, 15>(a, K, a.batch, c.smem, st);
-    default: return launch_cfg<V, 1024, 16, 4, 16>(a, K, a.batch, c.smem, st);
+    case 14: return launch_cfg<V, cluster_tpb(14), cluster_maxi(14), 4, 14>(a, K, a.batch, c.smem, st);
+    case 15: return launch_cfg<V, cluster_tpb(15), cluster_maxi(15), 4, 15>(a, K, a.batch, c.smem, st);
+    default: return launch_cfg<V, cluster_tpb(16), cluster_maxi(16), 4, 16>(a, K, a.batch, c.smem, st);
   }
 }
 

@@ -38,11 +38,11 @@ __host__ __device__ constexpr int small_tot_off(int logN) {
 template <int V>
 __device__ __noinline__ void ragged_small_item(const FusedArgs& a0, const SmallConsts& K, float* sm, int j0, int ntr,
                                                int c, const int* tlist) {
-  fused_body<V, 512, 16, 1, 0>(a0, K, sm, j0, ntr, c, region_stride(c), small_tot_off(c), tlist);
+  fused_body<V, SMALL_TPB, SMALL_MAXI, 1, 0>(a0, K, sm, j0, ntr, c, region_stride(c), small_tot_off(c), tlist);
 }
 
 template <int V>
-__global__ void __launch_bounds__(512, 1) ragged_small_kernel(const FusedArgs a0, const __grid_constant__ SmallConsts K,
+__global__ void __launch_bounds__(SMALL_TPB, 2) ragged_small_kernel(const FusedArgs a0, const __grid_constant__ SmallConsts K,
                                                            const RaggedArgs r) {
   extern __shared__ __align__(16) float sm[];
   __shared__ int s_item;
@@ -82,21 +82,22 @@ __global__ void __launch_bounds__(512, 1) ragged_small_kernel(const FusedArgs a0
   }
 }
 
-template <int V, int TPB, int LN>
-__global__ void __launch_bounds__(TPB) ragged_cluster_kernel(const FusedArgs a0, const __grid_constant__ SmallConsts K,
+template <int V, int LN, int TPB = cluster_tpb(LN)>
+__global__ void __launch_bounds__(TPB, TPB <= 256 ? 2 : 1) ragged_cluster_kernel(const FusedArgs a0, const __grid_constant__ SmallConsts K,
                                                              const RaggedArgs r) {
   extern __shared__ __align__(16) float sm[];
   const int n = r.cnt[LN];
   const int ncl = (int)(gridDim.x / 4);
   for (int j = (int)(blockIdx.x / 4); j < n; j += ncl)
-    fused_body<V, TPB, 16, 4, LN>(a0, K, sm, j, 1, LN, 0, a0.tot_off, r.list + LN * r.cap);
+    fused_body<V, TPB, cluster_maxi(LN), 4, LN>(a0, K, sm, j, 1, LN, 0, a0.tot_off, r.list + LN * r.cap);
 }
 
 // host: launch one persistent cluster grid for length 2^LN
-template <int V, int TPB, int LN>
+template <int V, int LN>
 cudaError_t ragged_cluster_launch(const FusedArgs& a, const SmallConsts& K, const RaggedArgs& r, int clusters,
                                   int smem, cudaStream_t st) {
-  auto kern = ragged_cluster_kernel<V, TPB, LN>;
+  constexpr int TPB = cluster_tpb(LN);
+  auto kern = ragged_cluster_kernel<V, LN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   cudaLaunchConfig_t cfg = {};
@@ -131,23 +132,23 @@ cudaError_t ragged_run(const FusedArgs& a0, const SmallConsts& K, const RaggedAr
     auto kern = ragged_small_kernel<V>;
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, L.small_smem);
     if (e != cudaSuccess) return e;
-    kern<<<(unsigned)L.small_grid, 512, L.small_smem, st>>>(a0, K, r);
+    kern<<<(unsigned)L.small_grid, SMALL_TPB, L.small_smem, st>>>(a0, K, r);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   FusedArgs a = a0;
   if (r.maxlog >= 14) {
     a.tot_off = L.cluster_tot_off[0];
-    e = ragged_cluster_launch<V, 256, 14>(a, K, r, L.clusters[0], L.cluster_smem[0], st);
+    e = ragged_cluster_launch<V, 14>(a, K, r, L.clusters[0], L.cluster_smem[0], st);
     if (e != cudaSuccess) return e;
   }
   if (r.maxlog >= 15) {
     a.tot_off = L.cluster_tot_off[1];
-    e = ragged_cluster_launch<V, 512, 15>(a, K, r, L.clusters[1], L.cluster_smem[1], st);
+    e = ragged_cluster_launch<V, 15>(a, K, r, L.clusters[1], L.cluster_smem[1], st);
     if (e != cudaSuccess) return e;
   }
   if (r.maxlog >= 16) {
     a.tot_off = L.cluster_tot_off[2];
-    e = ragged_cluster_launch<V, 1024, 16>(a, K, r, L.clusters[2], L.cluster_smem[2], st);
+    e = ragged_cluster_launch<V, 16>(a, K, r, L.clusters[2], L.cluster_smem[2], st);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -586,6 +586,102 @@ __device__ __forceinline__ void store_natural_cluster(float* sm, const FusedArgs
   }
 }
 
+// The tree and chain stages of the fused transform on the CTA's regions (g),
+// between the load and the store.  cctx: the region context on the cluster
+// path (LN > 0), where the final chain pair writes natural order.
+template <int V, int TPB, int MAXI, int CL, int LN>
+__device__ __forceinline__ void fused_compute(float* sm, const Geo& g, const float* __restrict__ ctab,
+                                              const SmallConsts& K, float* tot, float* wsum, float* snap, int cctx) {
+  const int logN = LN > 0 ? LN : g.logN, half = 1 << (logN - 1);
+  (void)tot;
+  (void)wsum;
+  (void)cctx;
+  const int logTop = logN - 2;  // log2 of the largest tree (N/4)
+  const BandPlan bp = band_plan(logN);
+  if constexpr (Var<V>::ot) {
+#pragma unroll
+    for (int b = 0; b < bp.nb; ++b) {
+      run_fold_band_r<V, TPB>(sm, g, bp.logL[b], bp.R[b], true, ctab);
+      __syncthreads();
+    }
+    {
+      const int nleaf = logTop >= LOG_LEAF ? ((half >> LOG_LEAF) - 1) : 0;
+      const int W = g.nreg * nleaf + g.nreg;
+      const Div dv(nleaf > 0 ? (unsigned)nleaf : 1u);
+      for (int w = threadIdx.x; w < W; w += TPB) {
+        if (w < g.nreg * nleaf) {
+          const int r = (int)dv((unsigned)w), b = w - r * nleaf;
+          const int p0 = b << LOG_LEAF;
+          run_leaf<V>(sm + r * g.RS, p0, node_ctx_g<V>(g, p0, LOG_LEAF, ctx_of(g, r)), K);
+        } else {
+          const int r = w - g.nreg * nleaf;
+          run_tail<V>(sm + r * g.RS, ctx_of(g, r), logN, K);
+        }
+      }
+      __syncthreads();
+    }
+    if constexpr (Var<V>::scan) {
+      for (int lp = LOG_LEAF + 1; lp <= logTop; ++lp) {
+        pass_recurrence<V, TPB, MAXI>(sm, tot, wsum, g, lp);
+        __syncthreads();
+      }
+    } else {
+#pragma unroll
+      for (int b = bp.nb - 1; b >= 0; --b) {
+        run_chunk_band_r<V, TPB>(sm, snap, g, bp.logL[b], bp.R[b]);
+        __syncthreads();
+      }
+    }
+    if constexpr (CL > 1 && LN > 0) {
+      // levels 2^7 .. 2^(LN-2) in pairs (a single level first when their
+      // count is odd), then the final pair (2^(LN-1), 2^LN) in natural order
+      constexpr int LO = LOG_LEAF + 2;
+      constexpr int LO2 = ((LN - 1 - LO) & 1) ? LO + 1 : LO;
+      const int ctx = cctx;
+      if constexpr (LO2 > LO) {
+        pass_chain<V, TPB, MAXI>(sm, g, LO);
+        __syncthreads();
+      }
+      chain_pairs<V, TPB, LN, LO2>(sm, half, ctx);
+      pass_chain2<V, TPB, LN - 1, true>(sm, half, ctx);
+    } else {
+      for (int lm = LOG_LEAF + 2; lm <= logN - 1; ++lm) {
+        pass_chain<V, TPB, MAXI>(sm, g, lm);
+        __syncthreads();
+      }
+    }
+  } else {
+    for (int lm = logN - 1; lm >= LOG_LEAF + 2; --lm) {
+      pass_chain<V, TPB, MAXI>(sm, g, lm);
+      __syncthreads();
+    }
+    for (int r = threadIdx.x; r < g.nreg; r += TPB) run_tail<V>(sm + r * g.RS, ctx_of(g, r), logN, K);
+    __syncthreads();
+    for (int lp = logTop; lp >= LOG_LEAF + 1; --lp) {
+      if constexpr (Var<V>::scan) pass_recurrence<V, TPB, MAXI>(sm, tot, wsum, g, lp);
+      else pass_neighbour<V, TPB, MAXI>(sm, g, lp);
+      __syncthreads();
+    }
+    if (logTop >= LOG_LEAF) {
+      const int nleaf = (half >> LOG_LEAF) - 1;
+      const int W = g.nreg * nleaf;
+      const Div dv((unsigned)nleaf);
+      for (int w = threadIdx.x; w < W; w += TPB) {
+        const int r = (int)dv((unsigned)w), b = w - r * nleaf;
+        const int p0 = b << LOG_LEAF;
+        run_leaf<V>(sm + r * g.RS, p0, node_ctx_g<V>(g, p0, LOG_LEAF, ctx_of(g, r)), K);
+      }
+      __syncthreads();
+    }
+#pragma unroll
+    for (int b = bp.nb - 1; b >= 0; --b) {
+      run_fold_band_r<V, TPB>(sm, g, bp.logL[b], bp.R[b], false, ctab);
+      __syncthreads();
+    }
+  }
+
+}
+
 // The fused transform of the CTA (cluster size 1: transforms at list
 // positions [j0, j0 + ntr)) or of the cluster (list position j0).  LN > 0:
 // compiled for log2 N = LN (every index computation is then resolved at
@@ -669,89 +765,8 @@ __device__ __forceinline__ void fused_body(const FusedArgs& a, const SmallConsts
   else cg::this_cluster().sync();
 
   // ---- trees and chain ----
-  const int logTop = logN - 2;  // log2 of the largest tree (N/4)
-  const BandPlan bp = band_plan(logN);
-  if constexpr (Var<V>::ot) {
-#pragma unroll
-    for (int b = 0; b < bp.nb; ++b) {
-      run_fold_band_r<V, TPB>(sm, g, bp.logL[b], bp.R[b], true, a.ctab);
-      __syncthreads();
-    }
-    {
-      const int nleaf = logTop >= LOG_LEAF ? ((half >> LOG_LEAF) - 1) : 0;
-      const int W = g.nreg * nleaf + g.nreg;
-      const Div dv(nleaf > 0 ? (unsigned)nleaf : 1u);
-      for (int w = threadIdx.x; w < W; w += TPB) {
-        if (w < g.nreg * nleaf) {
-          const int r = (int)dv((unsigned)w), b = w - r * nleaf;
-          const int p0 = b << LOG_LEAF;
-          run_leaf<V>(sm + r * g.RS, p0, node_ctx_g<V>(g, p0, LOG_LEAF, ctx_of(g, r)), K);
-        } else {
-          const int r = w - g.nreg * nleaf;
-          run_tail<V>(sm + r * g.RS, ctx_of(g, r), logN, K);
-        }
-      }
-      __syncthreads();
-    }
-    if constexpr (Var<V>::scan) {
-      for (int lp = LOG_LEAF + 1; lp <= logTop; ++lp) {
-        pass_recurrence<V, TPB, MAXI>(sm, tot, wsum, g, lp);
-        __syncthreads();
-      }
-    } else {
-#pragma unroll
-      for (int b = bp.nb - 1; b >= 0; --b) {
-        run_chunk_band_r<V, TPB>(sm, snap, g, bp.logL[b], bp.R[b]);
-        __syncthreads();
-      }
-    }
-    if constexpr (CL > 1 && LN > 0) {
-      // levels 2^7 .. 2^(LN-2) in pairs (a single level first when their
-      // count is odd), then the final pair (2^(LN-1), 2^LN) in natural order
-      constexpr int LO = LOG_LEAF + 2;
-      constexpr int LO2 = ((LN - 1 - LO) & 1) ? LO + 1 : LO;
-      const int ctx = (int)cg::this_cluster().block_rank() & 1;
-      if constexpr (LO2 > LO) {
-        pass_chain<V, TPB, MAXI>(sm, g, LO);
-        __syncthreads();
-      }
-      chain_pairs<V, TPB, LN, LO2>(sm, half, ctx);
-      pass_chain2<V, TPB, LN - 1, true>(sm, half, ctx);
-    } else {
-      for (int lm = LOG_LEAF + 2; lm <= logN - 1; ++lm) {
-        pass_chain<V, TPB, MAXI>(sm, g, lm);
-        __syncthreads();
-      }
-    }
-  } else {
-    for (int lm = logN - 1; lm >= LOG_LEAF + 2; --lm) {
-      pass_chain<V, TPB, MAXI>(sm, g, lm);
-      __syncthreads();
-    }
-    for (int r = threadIdx.x; r < g.nreg; r += TPB) run_tail<V>(sm + r * g.RS, ctx_of(g, r), logN, K);
-    __syncthreads();
-    for (int lp = logTop; lp >= LOG_LEAF + 1; --lp) {
-      if constexpr (Var<V>::scan) pass_recurrence<V, TPB, MAXI>(sm, tot, wsum, g, lp);
-      else pass_neighbour<V, TPB, MAXI>(sm, g, lp);
-      __syncthreads();
-    }
-    if (logTop >= LOG_LEAF) {
-      const int nleaf = (half >> LOG_LEAF) - 1;
-      const int W = g.nreg * nleaf;
-      const Div dv((unsigned)nleaf);
-      for (int w = threadIdx.x; w < W; w += TPB) {
-        const int r = (int)dv((unsigned)w), b = w - r * nleaf;
-        const int p0 = b << LOG_LEAF;
-        run_leaf<V>(sm + r * g.RS, p0, node_ctx_g<V>(g, p0, LOG_LEAF, ctx_of(g, r)), K);
-      }
-      __syncthreads();
-    }
-#pragma unroll
-    for (int b = bp.nb - 1; b >= 0; --b) {
-      run_fold_band_r<V, TPB>(sm, g, bp.logL[b], bp.R[b], false, a.ctab);
-      __syncthreads();
-    }
-  }
+  fused_compute<V, TPB, MAXI, CL, LN>(sm, g, a.ctab, K, tot, wsum, snap,
+                                      CL > 1 ? (int)cg::this_cluster().block_rank() & 1 : 0);
 
   // ---- store ----
   if constexpr (CL > 1 && LN > 0) {

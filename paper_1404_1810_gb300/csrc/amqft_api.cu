@@ -17,7 +17,7 @@
 
 namespace amqft {
 
-FusedConfig fused_config(int logN) {
+FusedConfig fused_config(int logN, int variant) {
   FusedConfig c;
   const int N = 1 << logN, half = N >> 1;
   c.RS = region_stride(logN);
@@ -32,7 +32,7 @@ FusedConfig fused_config(int logN) {
     c.per_cta = 1;
     c.nreg = 1;
     // 2^14, 2^15: 256 threads (two CTAs per SM); 2^16: 1024 threads, 32 values each
-    c.threads = cluster_tpb(logN);
+    c.threads = cluster_tpb(logN, variant_ot(variant));
   }
   c.tot_off = ((c.nreg * c.RS + 31) / 32) * 32;
   // scan scratch (threads + 32), snapshot, and one 16-bit exponent slot per transform
@@ -319,7 +319,7 @@ int amqft_plan(amqft_plan_t* out, int log2n, int variant, int64_t batch, int dty
     if (e != cudaSuccess) { free(h); cudaFree(p->d_ctab); delete p; return cuda_fail(e, "amqft_plan: cudaMemcpy"); }
   }
   free(h);
-  if (log2n >= 1 && log2n <= AMQFT_LOG2N_FUSED_MAX) p->cfg = fused_config(log2n);
+  if (log2n >= 1 && log2n <= AMQFT_LOG2N_FUSED_MAX) p->cfg = fused_config(log2n, variant);
   else memset(&p->cfg, 0, sizeof p->cfg);
   if (log2n > AMQFT_LOG2N_FUSED_MAX && batch > 0) {
     const long long half = N / 2;
@@ -606,7 +606,7 @@ int amqft_exec_ragged(amqft_plan_t p, int64_t count, const int64_t* d_offsets, c
     if (sm_bytes > L.small_smem) L.small_smem = sm_bytes;
   }
   for (int q = 0; q < 3; ++q) {
-    const FusedConfig fc = fused_config(14 + q);
+    const FusedConfig fc = fused_config(14 + q, p->variant);
     L.clusters[q] = (p->num_sms / 4) * p->knob[3];
     L.cluster_smem[q] = fc.smem;
     L.cluster_tot_off[q] = fc.tot_off;

@@ -123,12 +123,25 @@ __host__ __device__ constexpr int region_stride(int logN) {
 // 16384 region values (two CTAs per SM); 2^14..2^16: clusters of four CTAs,
 // one region each.  MAXI bounds the items a thread takes in the per-level
 // passes (MAXI * TPB must cover half a region).
+// ot: a time-first variant (1, 4, 5, 8), whose 2^14 kernel runs 128 threads
+// and four CTAs per SM (the harmonics-first variants' per-level neighbour
+// passes are faster with 256 threads).
 constexpr int SMALL_TPB = 256, SMALL_MAXI = 32;
-__host__ __device__ constexpr int cluster_tpb(int logN) { return logN == 16 ? 1024 : 256; }
-__host__ __device__ constexpr int cluster_maxi(int logN) { return logN == 15 ? 32 : 16; }
+__host__ __device__ constexpr bool variant_ot(int v) { return v == 1 || v == 4 || v == 5 || v == 8; }
+__host__ __device__ constexpr int cluster_tpb(int logN, bool ot) {
+  return logN == 16 ? 1024 : (logN == 14 && ot ? 128 : 256);
+}
+// items per thread that cover half a region (N/4) in the per-level passes, at least 16
+__host__ __device__ constexpr int cluster_maxi(int logN, bool ot) {
+  return (1 << (logN - 2)) / cluster_tpb(logN, ot) > 16 ? (1 << (logN - 2)) / cluster_tpb(logN, ot) : 16;
+}
+// CTAs per SM a kernel of TPB threads is compiled for (at most 128 registers a thread below 1024)
+__host__ __device__ constexpr int ctas_per_sm(int tpb) { return tpb <= 128 ? 4 : (tpb <= 256 ? 2 : 1); }
 static_assert(SMALL_TPB * SMALL_MAXI >= 8192, "per-level passes of the single-CTA path");
-static_assert(cluster_tpb(14) * cluster_maxi(14) >= (1 << 12) && cluster_tpb(15) * cluster_maxi(15) >= (1 << 13) &&
-                  cluster_tpb(16) * cluster_maxi(16) >= (1 << 14),
+static_assert(cluster_tpb(14, true) * cluster_maxi(14, true) >= (1 << 12) &&
+                  cluster_tpb(14, false) * cluster_maxi(14, false) >= (1 << 12) &&
+                  cluster_tpb(15, true) * cluster_maxi(15, true) >= (1 << 13) &&
+                  cluster_tpb(16, true) * cluster_maxi(16, true) >= (1 << 14),
               "per-level passes of the cluster path");
 
 // Context (0 DCT, 1 DST) of the tree node of size 2^logLp at region position p0.

@@ -850,7 +850,7 @@ __device__ __forceinline__ void fused_body(const FusedArgs& a, const SmallConsts
 }
 
 template <int V, int TPB, int MAXI, int CL, int LN>
-__global__ void __launch_bounds__(TPB, TPB <= 256 ? 2 : 1) fused_kernel(const FusedArgs a,
+__global__ void __launch_bounds__(TPB, ctas_per_sm(TPB)) fused_kernel(const FusedArgs a,
                                                                    const __grid_constant__ SmallConsts K) {
   extern __shared__ __align__(16) float sm[];
   if constexpr (CL == 1) {
@@ -899,9 +899,9 @@ cudaError_t launch_v(const FusedArgs& a, const SmallConsts& K, const FusedConfig
     return launch_cfg<V, SMALL_TPB, SMALL_MAXI, 1, 0>(a, K, grid, c.smem, st);
   }
   switch (a.logN) {
-    case 14: return launch_cfg<V, cluster_tpb(14), cluster_maxi(14), 4, 14>(a, K, a.batch, c.smem, st);
-    case 15: return launch_cfg<V, cluster_tpb(15), cluster_maxi(15), 4, 15>(a, K, a.batch, c.smem, st);
-    default: return launch_cfg<V, cluster_tpb(16), cluster_maxi(16), 4, 16>(a, K, a.batch, c.smem, st);
+    case 14: return launch_cfg<V, cluster_tpb(14, Var<V>::ot), cluster_maxi(14, Var<V>::ot), 4, 14>(a, K, a.batch, c.smem, st);
+    case 15: return launch_cfg<V, cluster_tpb(15, Var<V>::ot), cluster_maxi(15, Var<V>::ot), 4, 15>(a, K, a.batch, c.smem, st);
+    default: return launch_cfg<V, cluster_tpb(16, Var<V>::ot), cluster_maxi(16, Var<V>::ot), 4, 16>(a, K, a.batch, c.smem, st);
   }
 }
 

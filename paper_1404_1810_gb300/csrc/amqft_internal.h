@@ -24,7 +24,7 @@ struct FusedConfig {
   int tot_off;  // float offset of the scan scratch
 };
 
-FusedConfig fused_config(int logN);
+FusedConfig fused_config(int logN, int variant);
 
 cudaError_t launch_variant_1(const FusedArgs&, const SmallConsts&, const FusedConfig&, cudaStream_t);
 cudaError_t launch_variant_2(const FusedArgs&, const SmallConsts&, const FusedConfig&, cudaStream_t);

@@ -82,21 +82,21 @@ __global__ void __launch_bounds__(SMALL_TPB, 2) ragged_small_kernel(const FusedA
   }
 }
 
-template <int V, int LN, int TPB = cluster_tpb(LN)>
-__global__ void __launch_bounds__(TPB, TPB <= 256 ? 2 : 1) ragged_cluster_kernel(const FusedArgs a0, const __grid_constant__ SmallConsts K,
+template <int V, int LN, int TPB = cluster_tpb(LN, Var<V>::ot)>
+__global__ void __launch_bounds__(TPB, ctas_per_sm(TPB)) ragged_cluster_kernel(const FusedArgs a0, const __grid_constant__ SmallConsts K,
                                                              const RaggedArgs r) {
   extern __shared__ __align__(16) float sm[];
   const int n = r.cnt[LN];
   const int ncl = (int)(gridDim.x / 4);
   for (int j = (int)(blockIdx.x / 4); j < n; j += ncl)
-    fused_body<V, TPB, cluster_maxi(LN), 4, LN>(a0, K, sm, j, 1, LN, 0, a0.tot_off, r.list + LN * r.cap);
+    fused_body<V, TPB, cluster_maxi(LN, Var<V>::ot), 4, LN>(a0, K, sm, j, 1, LN, 0, a0.tot_off, r.list + LN * r.cap);
 }
 
 // host: launch one persistent cluster grid for length 2^LN
 template <int V, int LN>
 cudaError_t ragged_cluster_launch(const FusedArgs& a, const SmallConsts& K, const RaggedArgs& r, int clusters,
                                   int smem, cudaStream_t st) {
-  constexpr int TPB = cluster_tpb(LN);
+  constexpr int TPB = cluster_tpb(LN, Var<V>::ot);
   auto kern = ragged_cluster_kernel<V, LN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;

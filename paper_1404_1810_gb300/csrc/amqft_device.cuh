@@ -592,72 +592,6 @@ __device__ __forceinline__ int node_ctx_g(const Geo& g, int p0, int logLp, int c
   }
 }
 
-// D_k time phase + M_v time phase (ot variants) at node size 2^logLp, one
-// in-place quartet {i, L-1-i, H-1-i, H+i} of the node at p0.
-template <int V>
-__device__ __forceinline__ void fwd_ot_quartet(float* R, int p0, int logLp, int ctx, int i,
-                                               const float* __restrict__ ctab) {
-  const int Lp = 1 << logLp, H = Lp >> 1, i2 = H - 1 - i;
-  const float* __restrict__ ct = ctab + (H - 2);
-  const int pa = sw(p0 + i), pb = sw(p0 + Lp - 1 - i), pc = sw(p0 + i2), pd = sw(p0 + H + i);
-  const float u0 = R[pa], w0 = R[pb], u1 = R[pc], w1 = R[pd];
-  const float c0 = __ldg(ct + i), c1 = __ldg(ct + i2);
-  if (ctx == 0) {
-    R[pa] = u0 + w0; R[pd] = (u0 - w0) * c0;
-    R[pc] = u1 + w1; R[pb] = (u1 - w1) * c1;
-  } else {
-    R[pd] = u0 - w0; R[pa] = (u0 + w0) * c0;
-    R[pb] = u1 - w1; R[pc] = (u1 + w1) * c1;
-  }
-}
-
-// D_n frequency phase + M_v frequency phase (to variants), one in-place quartet.
-template <int V>
-__device__ __forceinline__ void bwd_to_quartet(float* R, int p0, int logLp, int ctx, int j,
-                                               const float* __restrict__ ctab) {
-  const int Lp = 1 << logLp, H = Lp >> 1, j2 = H - 1 - j;
-  const float* __restrict__ ct = ctab + (H - 2);
-  const int pa = sw(p0 + j), pb = sw(p0 + H + j), pc = sw(p0 + j2), pd = sw(p0 + Lp - 1 - j);
-  const float c0 = __ldg(ct + j), c1 = __ldg(ct + j2);
-  if (ctx == 0) {
-    const float e0 = R[pa], o0 = R[pb] * c0, e1 = R[pc], o1 = R[pd] * c1;
-    R[pa] = e0 + o0; R[pd] = e0 - o0;
-    R[pc] = e1 + o1; R[pb] = e1 - o1;
-  } else {
-    const float o0 = R[pa] * c0, e0 = R[pb], o1 = R[pc] * c1, e1 = R[pd];
-    R[pa] = o0 + e0; R[pd] = o0 - e0;
-    R[pc] = o1 + e1; R[pb] = o1 - e1;
-  }
-}
-
-template <int V, int TPB>
-__device__ __forceinline__ void pass_fwd_ot(float* sm, const Geo& g, int logLp, const float* __restrict__ ctab) {
-  const int logQ = logLp - 2, Q = 1 << logQ;
-  const unsigned nb = nodes_at(g, logLp);
-  const unsigned Wr = nb << logQ, W = Wr * (unsigned)g.nreg;
-  const Div dv(Wr);
-  for (unsigned w = threadIdx.x; w < W; w += TPB) {
-    const unsigned r = dv(w), rem = w - r * Wr;
-    const int p0 = (int)(rem >> logQ) << logLp;
-    fwd_ot_quartet<V>(sm + r * g.RS, p0, logLp, node_ctx_g<V>(g, p0, logLp, ctx_of(g, r)), (int)(rem & (Q - 1)),
-                      ctab);
-  }
-}
-
-template <int V, int TPB>
-__device__ __forceinline__ void pass_bwd_to(float* sm, const Geo& g, int logLp, const float* __restrict__ ctab) {
-  const int logQ = logLp - 2, Q = 1 << logQ;
-  const unsigned nb = nodes_at(g, logLp);
-  const unsigned Wr = nb << logQ, W = Wr * (unsigned)g.nreg;
-  const Div dv(Wr);
-  for (unsigned w = threadIdx.x; w < W; w += TPB) {
-    const unsigned r = dv(w), rem = w - r * Wr;
-    const int p0 = (int)(rem >> logQ) << logLp;
-    bwd_to_quartet<V>(sm + r * g.RS, p0, logLp, node_ctx_g<V>(g, p0, logLp, ctx_of(g, r)), (int)(rem & (Q - 1)),
-                      ctab);
-  }
-}
-
 // Neighbour form of M_v on the B half (bit-reversed order): the frequency
 // phase of M4/M8 (ot variants) or the time phase of M2/M6 (to variants).
 // Two phases: every thread reads, barrier, every thread writes.

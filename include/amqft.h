@@ -89,6 +89,18 @@ int amqft_exec_fwd(amqft_plan_t plan, const void *in, void *out, int32_t *exp_ou
 int amqft_exec_inv(amqft_plan_t plan, const void *in, const int32_t *exp_in, void *out,
                    int32_t *exp_out, void *stream);
 
+/* Real input (forward only): `batch` real signals of N = 2^log2n float32
+ * samples at in (signal j at [j*N, (j+1)*N)), their DFTs' harmonics 0 .. N/2
+ * (the rest follow by conjugate symmetry) to out, N/2 + 1 complex64 values
+ * per signal.  Two real signals a, b share one complex transform of a + ib:
+ * its regions C1, S1 and C2, S2 (Sect. 3.1-3.2) are the DCT-0 / DST-0 of a and
+ * of b, and R = DCT - i DST (Eq. qft_24-25), so the input costs 4 bytes a
+ * point.  Each harmonic equals the complex transform of the signal with a zero
+ * imaginary part.  N <= 2^AMQFT_LOG2N_FUSED_MAX; in 4-byte, out 8-byte aligned,
+ * not overlapping.  Errors: AMQFT_ERR_ARG, AMQFT_ERR_N, AMQFT_ERR_DTYPE (16-bit
+ * plans), AMQFT_ERR_ALIGN, AMQFT_ERR_INPLACE, AMQFT_ERR_CUDA. */
+int amqft_exec_rdft(amqft_plan_t plan, const float *in, void *out, void *stream);
+
 /* Transform the plan's batch from HOST memory to HOST memory: forward
  * (direction 0) or unnormalised inverse (direction 1) of `batch` complex64
  * transforms at in (read) and out (written), both host pointers, 8-byte

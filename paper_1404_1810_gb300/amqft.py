@@ -59,6 +59,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.amqft_ragged_tune.restype = i32
         lib.amqft_ragged_skipped.argtypes = [vp, ctypes.POINTER(i64)]
         lib.amqft_ragged_skipped.restype = i32
+        lib.amqft_exec_rdft.argtypes = [vp, vp, vp, vp]
+        lib.amqft_exec_rdft.restype = i32
         lib.amqft_exec_host.argtypes = [vp, vp, vp, i32, i64, vp]
         lib.amqft_exec_host.restype = i32
         lib.amqft_exec_static.argtypes = [vp, i64, vp, vp, i32, vp]
@@ -96,6 +98,10 @@ def amqft_exec_static(plan: int, batch: int, d_in: int, d_out: int, inverse: int
     no allocation in the call; calls overlapping in time on one device race."""
     _check(load().amqft_exec_static(plan, int(batch), d_in, d_out, int(inverse), stream or None),
            "amqft_exec_static")
+
+
+def amqft_exec_rdft(plan: int, d_in: int, d_out: int, stream: int = 0) -> None:
+    _check(load().amqft_exec_rdft(plan, d_in, d_out, stream or None), "amqft_exec_rdft")
 
 
 def amqft_exec_host(plan: int, h_in: int, h_out: int, direction: int = 0, chunk: int = 0, stream: int = 0) -> None:
@@ -230,6 +236,21 @@ class Plan:
         amqft_exec_inv(self.handle, x.data_ptr(), exp_in.data_ptr() if exp_in is not None else 0, out.data_ptr(),
                        exp_out.data_ptr(), _stream_handle(stream))
         return out, exp_out
+
+    def rdft(self, x, out=None, stream=None):
+        """Harmonics 0 .. N/2 of `batch` real float32 signals (batch, N) -> (batch, N/2 + 1) complex64."""
+        import torch
+
+        if self.dtype != AMQFT_C64:
+            raise ValueError("rdft needs a complex64 plan")
+        if x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous() or x.numel() != self.batch * self.n:
+            raise ValueError(f"x must be a contiguous float32 CUDA tensor of {self.batch} x {self.n}")
+        if out is None:
+            out = torch.empty((self.batch, self.n // 2 + 1), dtype=torch.complex64, device=x.device)
+        if out.dtype != torch.complex64 or not out.is_contiguous() or out.numel() != self.batch * (self.n // 2 + 1):
+            raise ValueError("out must be a contiguous complex64 tensor of batch x (N/2 + 1)")
+        amqft_exec_rdft(self.handle, x.data_ptr(), out.data_ptr(), _stream_handle(stream))
+        return out
 
     def _host(self, x, out, inverse, chunk, stream):
         import torch

@@ -112,6 +112,12 @@ __global__ void copy1_kernel(const float2* __restrict__ in, float2* __restrict__
   if (i < batch) out[i] = in[i];
 }
 
+// N = 1, real input: R(0) = x(0).
+__global__ void copy1_real_kernel(const float* __restrict__ in, float2* __restrict__ out, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = make_float2(in[i], 0.f);
+}
+
 // N = 1 with 16-bit storage: the value (conjugated for the inverse) gets the
 // exponent of its largest component, like every other length.
 __global__ void copy1_16_kernel(const unsigned* __restrict__ in, unsigned* __restrict__ out,
@@ -407,6 +413,7 @@ static int exec_n(amqft_plan_t p, long long batch, const void* in, void* out, in
   a.tot_off = p->cfg.tot_off;
   a.tlist = nullptr;
   a.toff = nullptr;
+  a.nreal = 0;
   e = fused_launch(p->variant, a, p->small, p->cfg, st);
   if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
   return AMQFT_OK;
@@ -423,6 +430,46 @@ int amqft_exec_inv(amqft_plan_t p, const void* in, const int32_t* exp_in, void* 
   t_err.clear();
   if (!p) return fail(AMQFT_ERR_ARG, "plan is NULL");
   return exec_n(p, p->batch, in, out, 1, exp_in, exp_out, stream);
+}
+
+int amqft_exec_rdft(amqft_plan_t p, const float* in, void* out, void* stream) {
+  t_err.clear();
+  if (!p) return fail(AMQFT_ERR_ARG, "plan is NULL");
+  if (p->ragged) return fail(AMQFT_ERR_ARG, "amqft_exec_rdft: not for ragged plans");
+  if (p->dtype != AMQFT_C64) return fail(AMQFT_ERR_DTYPE, "amqft_exec_rdft: AMQFT_C64 plans only");
+  if (p->log2n > AMQFT_LOG2N_FUSED_MAX)
+    return fail(AMQFT_ERR_N, "amqft_exec_rdft: log2n=%d above %d (real input runs on the fused kernels)", p->log2n,
+                AMQFT_LOG2N_FUSED_MAX);
+  if (p->batch == 0) return AMQFT_OK;
+  if (!in || !out) return fail(AMQFT_ERR_ALIGN, "amqft_exec_rdft: in or out is NULL");
+  if (((uintptr_t)in & 3u) || ((uintptr_t)out & 7u))
+    return fail(AMQFT_ERR_ALIGN, "amqft_exec_rdft: in must be 4-byte and out 8-byte aligned");
+  const long long N = 1LL << p->log2n;
+  const uintptr_t a0 = (uintptr_t)in, b0 = (uintptr_t)out;
+  const uintptr_t ia = (uintptr_t)(N * p->batch * 4), ob = (uintptr_t)((N / 2 + 1) * p->batch * 8);
+  if (a0 < b0 + ob && b0 < a0 + ia) return fail(AMQFT_ERR_INPLACE, "amqft_exec_rdft: in and out overlap");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  if (p->log2n == 0) {
+    copy1_real_kernel<<<(unsigned)((p->batch + 255) / 256), 256, 0, st>>>(in, (float2*)out, p->batch);
+    e = cudaGetLastError();
+    return e == cudaSuccess ? AMQFT_OK : cuda_fail(e, "copy kernel launch");
+  }
+  FusedArgs a;
+  memset(&a, 0, sizeof a);
+  a.in = in;
+  a.out = out;
+  a.dtype = AMQFT_C64;
+  a.ctab = p->d_ctab;
+  a.batch = (p->batch + 1) / 2;  // one complex transform per pair of real signals
+  a.nreal = p->batch;
+  a.logN = p->log2n;
+  a.tpc = p->cfg.per_cta;
+  a.RS = p->cfg.RS;
+  a.tot_off = p->cfg.tot_off;
+  e = fused_launch(p->variant, a, p->small, p->cfg, st);
+  if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
+  return AMQFT_OK;
 }
 
 // Host-memory execution: staging on the device, three internal streams.

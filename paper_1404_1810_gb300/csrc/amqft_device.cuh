@@ -73,6 +73,9 @@ struct FusedArgs {
   int tot_off;         // float offset of the scan scratch in shared memory
   const int* tlist;    // transform ids by list position (NULL: the position itself)
   const long long* toff;  // element offset of each transform id (NULL: id * N)
+  long long nreal;     // > 0: real input, transform t = real signals 2t and 2t+1
+                       // (float32, N each, the second absent past nreal); out holds
+                       // the N/2 + 1 harmonics of every signal (forward only)
 };
 
 template <int V>

@@ -124,6 +124,34 @@ __device__ __forceinline__ Fetched load_fetch(const InRef& in, int logN, long lo
   return f;
 }
 
+// Real input: samples n, N-n, N/2-n, N/2+n of real signals 2t (as the real
+// part) and 2t+1 (as the imaginary part, zero past nreal).  The complex
+// transform of a + ib then holds the DCT-0 / DST-0 of a in regions C1 / S1 and
+// those of b in C2 / S2 (Sect. 3.1).
+__device__ __forceinline__ Fetched load_fetch_real(const float* __restrict__ in, int logN, long long t,
+                                                   long long nreal, int n) {
+  const int N = 1 << logN, half = N >> 1, Q = N >> 2;
+  const float* __restrict__ za = in + (2 * t) * (long long)N;
+  const bool hb = 2 * t + 1 < nreal;
+  const float* __restrict__ zb = za + N;
+  auto ld = [&](int i) { return make_float2(__ldcs(za + i), hb ? __ldcs(zb + i) : 0.f); };
+  Fetched f;
+  if (n == 0) {
+    f.a = ld(0);
+    f.b = ld(half);
+    if (N >= 4) {
+      f.c = ld(Q);
+      f.d = ld(3 * Q);
+    }
+  } else {
+    f.a = ld(n);
+    f.b = ld(N - n);
+    f.c = ld(half - n);
+    f.d = ld(half + n);
+  }
+  return f;
+}
+
 template <int V, class RG>
 __device__ __forceinline__ void load_scatter(const RG& rg, int logN, int tau, int n, const Fetched& f) {
   const int N = 1 << logN, half = N >> 1, Q = N >> 2, logQ = logN - 2;
@@ -269,6 +297,58 @@ __device__ __forceinline__ Out4 emit_values(int logN, int k, const Gathered& g) 
   o.v[2] = make_float2(cm1 + sm2, cm2 - sm1); o.i[2] = m;
   o.v[3] = make_float2(cm1 - sm2, cm2 + sm1); o.i[3] = half + k;
   return o;
+}
+
+// Real input, orbit item k: harmonics k and N/2 - k (item 0: 0, N/2, N/4)
+// of both signals of the pair, R = DCT - i DST (Eq. qft_24-25), written to the
+// half spectra (N/2 + 1 values each) of signals 2t and 2t+1.
+template <int V>
+__device__ __forceinline__ void store_real(float2* __restrict__ out, int logN, long long t, long long nreal, int k,
+                                           const Gathered& g) {
+  const int N = 1 << logN, half = N >> 1, Q = N >> 2;
+  float2* __restrict__ ra = out + (2 * t) * (long long)(half + 1);
+  float2* __restrict__ rb = ra + (half + 1);
+  const bool hb = 2 * t + 1 < nreal;
+  if (k == 0) {
+    if (N == 2) {
+      __stcs(ra, make_float2(g.v[0], 0.f));
+      __stcs(ra + 1, make_float2(g.v[1], 0.f));
+      if (hb) {
+        __stcs(rb, make_float2(g.v[2], 0.f));
+        __stcs(rb + 1, make_float2(g.v[3], 0.f));
+      }
+      return;
+    }
+    float c01, c02, ch1, ch2;
+    if constexpr (Var<V>::ot) {
+      c01 = g.v[0] + g.v[1]; ch1 = g.v[0] - g.v[1]; c02 = g.v[2] + g.v[3]; ch2 = g.v[2] - g.v[3];
+    } else {
+      c01 = g.v[0]; ch1 = g.v[1]; c02 = g.v[2]; ch2 = g.v[3];
+    }
+    __stcs(ra, make_float2(c01, 0.f));
+    __stcs(ra + half, make_float2(ch1, 0.f));
+    __stcs(ra + Q, make_float2(g.v[4], -g.v[6]));
+    if (hb) {
+      __stcs(rb, make_float2(c02, 0.f));
+      __stcs(rb + half, make_float2(ch2, 0.f));
+      __stcs(rb + Q, make_float2(g.v[5], -g.v[7]));
+    }
+    return;
+  }
+  float ck1, ck2, cm1, cm2, sk1, sk2, sm1, sm2;
+  if constexpr (Var<V>::ot) {
+    ck1 = g.v[0] + g.v[1]; cm1 = g.v[0] - g.v[1]; ck2 = g.v[2] + g.v[3]; cm2 = g.v[2] - g.v[3];
+    sk1 = g.v[4] + g.v[5]; sm1 = g.v[4] - g.v[5]; sk2 = g.v[6] + g.v[7]; sm2 = g.v[6] - g.v[7];
+  } else {
+    ck1 = g.v[0]; cm1 = g.v[1]; ck2 = g.v[2]; cm2 = g.v[3];
+    sk1 = g.v[4]; sm1 = g.v[5]; sk2 = g.v[6]; sm2 = g.v[7];
+  }
+  __stcs(ra + k, make_float2(ck1, -sk1));
+  __stcs(ra + (half - k), make_float2(cm1, -sm1));
+  if (hb) {
+    __stcs(rb + k, make_float2(ck2, -sk2));
+    __stcs(rb + (half - k), make_float2(cm2, -sm2));
+  }
 }
 
 __device__ __forceinline__ float out4_absmax(const Out4& o) {
@@ -498,6 +578,25 @@ __device__ __forceinline__ void store_natural_cluster(float* sm, const FusedArgs
   static_assert(NG * 4 * TPB == PER, "four harmonics per thread and step");
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
+  if (a.nreal > 0) {
+    // real input: R = DCT - i DST of each signal of the pair, harmonics 0 .. N/2
+    float2* __restrict__ ra = static_cast<float2*>(a.out) + (2 * t) * (long long)(half + 1);
+    float2* __restrict__ rb = ra + (half + 1);
+    const bool hb = 2 * t + 1 < a.nreal;
+    const float* c1 = cl.map_shared_rank(sm, 0);
+    const float* s1 = cl.map_shared_rank(sm, 1);
+    const float* c2 = cl.map_shared_rank(sm, 2);
+    const float* s2 = cl.map_shared_rank(sm, 3);
+    for (int k = rank * PER + (int)threadIdx.x; k < (rank + 1) * PER; k += TPB) {
+      __stcs(ra + k, make_float2(c1[k], k == 0 ? 0.f : -s1[k]));
+      if (hb) __stcs(rb + k, make_float2(c2[k], k == 0 ? 0.f : -s2[k]));
+    }
+    if (rank == 0 && threadIdx.x == 0) {
+      __stcs(ra + half, make_float2(c1[half], 0.f));
+      if (hb) __stcs(rb + half, make_float2(c2[half], 0.f));
+    }
+    return;
+  }
   const float4* C1 = reinterpret_cast<const float4*>(cl.map_shared_rank(sm, 0));
   const float4* S1 = reinterpret_cast<const float4*>(cl.map_shared_rank(sm, 1));
   const float4* C2 = reinterpret_cast<const float4*>(cl.map_shared_rank(sm, 2));
@@ -754,7 +853,8 @@ __device__ __forceinline__ void fused_body(const FusedArgs& a, const SmallConsts
       }
       if (ok_[s]) {
         const long long t = tid(tau_[s]);
-        f_[s] = load_fetch(InRef{a.in, a.exp_in, a.dtype}, logN, t, toff(t), n_[s], cj);
+        f_[s] = a.nreal > 0 ? load_fetch_real(static_cast<const float*>(a.in), logN, t, a.nreal, n_[s])
+                            : load_fetch(InRef{a.in, a.exp_in, a.dtype}, logN, t, toff(t), n_[s], cj);
       }
     }
 #pragma unroll
@@ -835,7 +935,9 @@ __device__ __forceinline__ void fused_body(const FusedArgs& a, const SmallConsts
       for (int s = 0; s < U; ++s) {
         if (!ok_[s]) continue;
         const long long t = tid(tau_[s]);
-        if (c64) {
+        if (a.nreal > 0) {
+          store_real<V>(static_cast<float2*>(a.out), logN, t, a.nreal, k_[s], g_[s]);
+        } else if (c64) {
           store_emit<V>(static_cast<float2*>(a.out), logN, toff(t), k_[s], g_[s], cj);
         } else {
           const int e = block_exponent(__int_as_float(slot[tau_[s]]));

@@ -1,0 +1,52 @@
+"""Host-side logic that needs no GPU: the autotuner's cache and batch
+signature, 16-bit dequantisation, and that the library refuses to run without
+a CUDA device (there is no CPU fallback)."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import synth
+
+
+def test_batch_signature_counts_lengths():
+    from paper_1404_1810_gb300.autotune import batch_signature
+
+    lg = torch.tensor([4, 4, 18, 0, 4], dtype=torch.uint8)
+    sig = batch_signature(lg).split(",")
+    assert len(sig) == 32
+    assert sig[4] == "3" and sig[18] == "1" and sig[0] == "1" and sig[5] == "0"
+
+
+def test_autotune_cache_roundtrip(tmp_path):
+    from paper_1404_1810_gb300.autotune import _load_cache, _save_cache
+
+    path = str(tmp_path / "sub" / "tune.json")
+    assert _load_cache(path) == {}
+    _save_cache(path, {"k": {"knobs": {"schedule": 1}, "ms": 1.5}})
+    assert _load_cache(path)["k"]["knobs"]["schedule"] == 1
+    with open(path, "w") as f:
+        f.write("not json")
+    assert _load_cache(path) == {}      # a damaged cache is ignored, not fatal
+
+
+@pytest.mark.parametrize("dt", [torch.bfloat16, torch.float16])
+def test_dequantize_scales_by_two_to_the_exponent(dt):
+    from paper_1404_1810_gb300 import dequantize
+
+    x = synth.normal_complex(64, 3, config=3)
+    v = torch.view_as_real(torch.from_numpy(x)).to(dt)
+    e = torch.tensor([0, 5, -7], dtype=torch.int32)
+    got = dequantize(v, e).numpy()
+    want = torch.view_as_complex(v.double()).numpy() * (2.0 ** e.numpy().astype(np.float64))[:, None]
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.skipif(torch.cuda.is_available(), reason="checks the behaviour without a GPU")
+def test_no_cpu_fallback():
+    from paper_1404_1810_gb300 import AmqftError, Plan, build
+
+    build.build()
+    with pytest.raises(AmqftError):
+        Plan(10, 4, 1)                  # no CUDA device: the plan cannot be made

@@ -135,6 +135,14 @@ const char *amqft_version(void);
  * Any out pointer may be NULL. */
 int amqft_plan_info(amqft_plan_t plan, int *cluster, int *per_cta, int *threads, int *smem_bytes);
 
+/* Number of kernels the library has launched for exec calls on this plan
+ * (amqft_exec_fwd / inv / host / rdft / ragged / static) since it was made:
+ * a host-side count of launches that were accepted by the CUDA runtime, for
+ * benchmarks that report how many kernels a step runs.  Memsets and copies are
+ * not kernels and are not counted.  Returns the count (>= 0), or
+ * AMQFT_ERR_ARG for a NULL plan. */
+int64_t amqft_plan_launches(amqft_plan_t plan);
+
 /* ---------------------------------------------------------------------
  * Ragged batches: many transforms of different power-of-two lengths, each at
  * its own offset, in one call that launches a fixed sequence of kernels and

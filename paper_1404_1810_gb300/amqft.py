@@ -67,6 +67,8 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.amqft_exec_static.restype = i32
         lib.amqft_plan_info.argtypes = [vp] + [ctypes.POINTER(i32)] * 4
         lib.amqft_plan_info.restype = i32
+        lib.amqft_plan_launches.argtypes = [vp]
+        lib.amqft_plan_launches.restype = i64
         _lib = lib
         return lib
 
@@ -149,6 +151,14 @@ def amqft_plan_info(plan: int) -> dict:
     return dict(zip(("cluster", "per_cta", "threads", "smem_bytes"), (v.value for v in vals)))
 
 
+def amqft_plan_launches(plan: int) -> int:
+    """Kernels the library has launched for exec calls on this plan so far."""
+    n = int(load().amqft_plan_launches(plan))
+    if n < 0:
+        _check(n, "amqft_plan_launches")
+    return n
+
+
 # --- torch convenience layer ------------------------------------------------
 
 def _stream_handle(stream) -> int:
@@ -178,6 +188,10 @@ class Plan:
 
     def info(self) -> dict:
         return amqft_plan_info(self.handle)
+
+    def launches(self) -> int:
+        """Kernels launched by this plan's exec calls so far."""
+        return amqft_plan_launches(self.handle)
 
     def _check_tensor(self, t, name):
         import torch
@@ -317,6 +331,10 @@ class RaggedPlan:
         amqft_exec_ragged(self.handle, log2n.numel(), offsets.data_ptr(), log2n.data_ptr(), x.data_ptr(),
                           out.data_ptr(), 1 if inverse else 0, _stream_handle(stream))
         return out
+
+    def launches(self) -> int:
+        """Kernels launched by this plan's exec calls so far."""
+        return amqft_plan_launches(self.handle)
 
     def skipped(self) -> int:
         return amqft_ragged_skipped(self.handle)

@@ -3,6 +3,7 @@
 // except the trig-constant table of a plan.
 #include <math.h>
 #include <stdarg.h>
+#include <atomic>
 #include <new>
 #include <stdint.h>
 #include <stdio.h>
@@ -55,16 +56,16 @@ static cudaError_t fused_launch(int variant, const FusedArgs& a, const SmallCons
 }
 
 static cudaError_t ragged_launch(int variant, const FusedArgs& a, const SmallConsts& K, const RaggedArgs& r,
-                                 const RaggedLaunch& L, cudaStream_t st) {
+                                 const RaggedLaunch& L, cudaStream_t st, long long* nl) {
   switch (variant) {
-    case 1: return ragged_variant_1(a, K, r, L, st);
-    case 2: return ragged_variant_2(a, K, r, L, st);
-    case 3: return ragged_variant_3(a, K, r, L, st);
-    case 4: return ragged_variant_4(a, K, r, L, st);
-    case 5: return ragged_variant_5(a, K, r, L, st);
-    case 6: return ragged_variant_6(a, K, r, L, st);
-    case 7: return ragged_variant_7(a, K, r, L, st);
-    default: return ragged_variant_8(a, K, r, L, st);
+    case 1: return ragged_variant_1(a, K, r, L, st, nl);
+    case 2: return ragged_variant_2(a, K, r, L, st, nl);
+    case 3: return ragged_variant_3(a, K, r, L, st, nl);
+    case 4: return ragged_variant_4(a, K, r, L, st, nl);
+    case 5: return ragged_variant_5(a, K, r, L, st, nl);
+    case 6: return ragged_variant_6(a, K, r, L, st, nl);
+    case 7: return ragged_variant_7(a, K, r, L, st, nl);
+    default: return ragged_variant_8(a, K, r, L, st, nl);
   }
 }
 
@@ -97,12 +98,12 @@ __global__ void ragged_bucket_kernel(const unsigned char* __restrict__ log2n, co
 
 
 static cudaError_t multipass_launch(int variant, const MpArgs& a, float* W0, float* W1, const SmallConsts& K,
-                                    cudaStream_t st) {
+                                    cudaStream_t st, long long* nl) {
   switch (variant) {
-    case 2: return multipass_variant_2(a, W0, W1, K, st);
-    case 4: return multipass_variant_4(a, W0, W1, K, st);
-    case 6: return multipass_variant_6(a, W0, W1, K, st);
-    default: return multipass_variant_8(a, W0, W1, K, st);
+    case 2: return multipass_variant_2(a, W0, W1, K, st, nl);
+    case 4: return multipass_variant_4(a, W0, W1, K, st, nl);
+    case 6: return multipass_variant_6(a, W0, W1, K, st, nl);
+    default: return multipass_variant_8(a, W0, W1, K, st, nl);
   }
 }
 
@@ -219,6 +220,8 @@ struct amqft_plan_s {
   void* h_buf[4];
   cudaStream_t h_st[3];
   cudaEvent_t h_ev[8];
+  // kernels launched by the exec calls on this plan (amqft_plan_launches)
+  std::atomic<long long> launches{0};
 };
 
 // workspace budget of one plan (both ping-pong buffers)
@@ -235,6 +238,10 @@ int plan_view(amqft_plan_t p, PlanView* v) {
   v->ctab = p->d_ctab;
   v->small = &p->small;
   return AMQFT_OK;
+}
+
+void add_launches(amqft_plan_t p, long long n) {
+  if (p) p->launches += n;
 }
 
 int set_error(int code, const char* fmt, ...) {
@@ -384,7 +391,9 @@ static int exec_n(amqft_plan_t p, long long batch, const void* in, void* out, in
       a.tlist = nullptr;
       a.toff = nullptr;
       a.ntdev = nullptr;
-      e = multipass_launch(p->variant, a, p->d_work, p->d_work + per_buf, p->small, st);
+      long long nl = 0;
+      e = multipass_launch(p->variant, a, p->d_work, p->d_work + per_buf, p->small, st, &nl);
+      p->launches += nl;
       if (e != cudaSuccess) return cuda_fail(e, "multi-pass launch");
     }
     return AMQFT_OK;
@@ -396,6 +405,7 @@ static int exec_n(amqft_plan_t p, long long batch, const void* in, void* out, in
                                                p->dtype);
     e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "copy kernel launch");
+    ++p->launches;
     return AMQFT_OK;
   }
   FusedArgs a;
@@ -416,6 +426,7 @@ static int exec_n(amqft_plan_t p, long long batch, const void* in, void* out, in
   a.nreal = 0;
   e = fused_launch(p->variant, a, p->small, p->cfg, st);
   if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
+  ++p->launches;
   return AMQFT_OK;
 }
 
@@ -453,7 +464,9 @@ int amqft_exec_rdft(amqft_plan_t p, const float* in, void* out, void* stream) {
   if (p->log2n == 0) {
     copy1_real_kernel<<<(unsigned)((p->batch + 255) / 256), 256, 0, st>>>(in, (float2*)out, p->batch);
     e = cudaGetLastError();
-    return e == cudaSuccess ? AMQFT_OK : cuda_fail(e, "copy kernel launch");
+    if (e != cudaSuccess) return cuda_fail(e, "copy kernel launch");
+    ++p->launches;
+    return AMQFT_OK;
   }
   FusedArgs a;
   memset(&a, 0, sizeof a);
@@ -469,6 +482,7 @@ int amqft_exec_rdft(amqft_plan_t p, const float* in, void* out, void* stream) {
   a.tot_off = p->cfg.tot_off;
   e = fused_launch(p->variant, a, p->small, p->cfg, st);
   if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
+  ++p->launches;
   return AMQFT_OK;
 }
 
@@ -626,6 +640,7 @@ int amqft_exec_ragged(amqft_plan_t p, int64_t count, const int64_t* d_offsets, c
                                                            p->max_points, p->d_rcnt, p->d_rlist, p->max_count,
                                                            p->d_rcnt + 33, (const float2*)in, (float2*)out);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "ragged bucket launch");
+    ++p->launches;
   }
   FusedArgs a;
   memset(&a, 0, sizeof a);
@@ -658,7 +673,9 @@ int amqft_exec_ragged(amqft_plan_t p, int64_t count, const int64_t* d_offsets, c
     L.cluster_smem[q] = fc.smem;
     L.cluster_tot_off[q] = fc.tot_off;
   }
-  e = ragged_launch(p->variant, a, p->small, r, L, st);
+  long long nl = 0;
+  e = ragged_launch(p->variant, a, p->small, r, L, st, &nl);
+  p->launches += nl;
   if (e != cudaSuccess) return cuda_fail(e, "ragged launch");
   for (int c = AMQFT_LOG2N_FUSED_MAX + 1; c <= p->log2n; ++c) {
     const long long capc = ragged_capacity(p, c);
@@ -678,7 +695,9 @@ int amqft_exec_ragged(amqft_plan_t p, int64_t count, const int64_t* d_offsets, c
     m.tlist = p->d_rlist + (long long)c * p->max_count;
     m.toff = (const long long*)d_offsets;
     m.ntdev = p->d_rcnt + c;
-    e = multipass_launch(p->variant, m, p->d_rwork, p->d_rwork + capc * 4 * RSg, p->small, st);
+    nl = 0;
+    e = multipass_launch(p->variant, m, p->d_rwork, p->d_rwork + capc * 4 * RSg, p->small, st, &nl);
+    p->launches += nl;
     if (e != cudaSuccess) return cuda_fail(e, "ragged multi-pass launch");
   }
   return AMQFT_OK;
@@ -704,6 +723,12 @@ int amqft_ragged_skipped(amqft_plan_t p, int64_t* skipped) {
   if (e != cudaSuccess) return cuda_fail(e, "amqft_ragged_skipped: cudaMemcpy");
   *skipped = v;
   return AMQFT_OK;
+}
+
+int64_t amqft_plan_launches(amqft_plan_t p) {
+  t_err.clear();
+  if (!p) return fail(AMQFT_ERR_ARG, "plan is NULL");
+  return (int64_t)p->launches.load();
 }
 
 int amqft_plan_info(amqft_plan_t p, int* cluster, int* per_cta, int* threads, int* smem_bytes) {

@@ -299,15 +299,17 @@ __device__ __forceinline__ void run_chunk_band(float* sm, float* snap, const Geo
   const unsigned total = per * (unsigned)g.nreg;
   const Div dv(per);
   const int lane = threadIdx.x & 31;
-  // pass 1: snapshot of the run ends
-  for (unsigned w = threadIdx.x; w < total; w += TPB) {
-    if (lane != 0 && lane != 31) continue;
+  // pass 1: snapshot of the run ends, one thread per end (entry e: run e / 2,
+  // first lane for even e, last lane for odd e)
+  const unsigned ends = total >> 4;
+  for (unsigned e = threadIdx.x; e < ends; e += TPB) {
+    const unsigned w = ((e >> 1) << 5) | ((e & 1u) ? 31u : 0u);
     const unsigned r = dv(w), it = w - r * per;
     const float* Rg = sm + (long long)r * g.RS;
     const int c0 = ctx_of(g, r);
     const unsigned b = it >> logW;
-    const int q = (int)(it & (unsigned)(W - 1)), m = q;
-    float* dst = snap + ((w >> 5) * 2 + (lane == 31)) * NSLOT;
+    const int m = (int)(it & (unsigned)(W - 1));
+    float* dst = snap + e * NSLOT;
     if (b < nb0) {
       const int p0 = (int)(b << logL);
       if (node_ctx_g<V>(g, p0, logL, c0) == 0) snap_item<V, R, 0, 0>(Rg, p0, logL, m, dst);

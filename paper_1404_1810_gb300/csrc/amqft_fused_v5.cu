@@ -7,7 +7,7 @@ cudaError_t launch_variant_5(const FusedArgs& a, const SmallConsts& K, const Fus
   return launch_v<5>(a, K, c, st);
 }
 cudaError_t ragged_variant_5(const FusedArgs& a, const SmallConsts& K, const RaggedArgs& r, const RaggedLaunch& L,
-                               cudaStream_t st) {
-  return ragged_run<5>(a, K, r, L, st);
+                               cudaStream_t st, long long* nlaunch) {
+  return ragged_run<5>(a, K, r, L, st, nlaunch);
 }
 }  // namespace amqft

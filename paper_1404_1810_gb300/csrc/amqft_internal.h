@@ -35,21 +35,30 @@ cudaError_t launch_variant_6(const FusedArgs&, const SmallConsts&, const FusedCo
 cudaError_t launch_variant_7(const FusedArgs&, const SmallConsts&, const FusedConfig&, cudaStream_t);
 cudaError_t launch_variant_8(const FusedArgs&, const SmallConsts&, const FusedConfig&, cudaStream_t);
 
-// ragged batches (every length up to the plan's), all variants
-cudaError_t ragged_variant_1(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t);
-cudaError_t ragged_variant_2(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t);
-cudaError_t ragged_variant_3(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t);
-cudaError_t ragged_variant_4(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t);
-cudaError_t ragged_variant_5(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t);
-cudaError_t ragged_variant_6(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t);
-cudaError_t ragged_variant_7(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t);
-cudaError_t ragged_variant_8(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t);
+// ragged batches (every length up to the plan's), all variants; the ragged and
+// multi-pass sequences add the kernels they launch to *nlaunch (may be NULL)
+cudaError_t ragged_variant_1(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t,
+                             long long* nlaunch);
+cudaError_t ragged_variant_2(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t,
+                             long long* nlaunch);
+cudaError_t ragged_variant_3(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t,
+                             long long* nlaunch);
+cudaError_t ragged_variant_4(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t,
+                             long long* nlaunch);
+cudaError_t ragged_variant_5(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t,
+                             long long* nlaunch);
+cudaError_t ragged_variant_6(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t,
+                             long long* nlaunch);
+cudaError_t ragged_variant_7(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t,
+                             long long* nlaunch);
+cudaError_t ragged_variant_8(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t,
+                             long long* nlaunch);
 
 // multi-pass path (2^17 <= N <= 2^24), variants 2, 4, 6, 8
-cudaError_t multipass_variant_2(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t);
-cudaError_t multipass_variant_4(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t);
-cudaError_t multipass_variant_6(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t);
-cudaError_t multipass_variant_8(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t);
+cudaError_t multipass_variant_2(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t, long long* nlaunch);
+cudaError_t multipass_variant_4(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t, long long* nlaunch);
+cudaError_t multipass_variant_6(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t, long long* nlaunch);
+cudaError_t multipass_variant_8(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t, long long* nlaunch);
 
 // Read-only view of a plan, for entry points defined outside the plan's
 // translation unit.  Returns AMQFT_ERR_ARG for a NULL plan.
@@ -62,6 +71,9 @@ struct PlanView {
   const SmallConsts* small;  // host copy of the leaf constants
 };
 int plan_view(amqft_plan_t plan, PlanView* v);
+
+// Add n to the plan's count of launched kernels (amqft_plan_launches).
+void add_launches(amqft_plan_t plan, long long n);
 
 // Record the calling thread's error message (amqft_last_error) and return code.
 int set_error(int code, const char* fmt, ...);

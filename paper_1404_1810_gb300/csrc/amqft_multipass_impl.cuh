@@ -384,9 +384,15 @@ inline int mp_solve_smem_bytes() {
 }
 
 // Host side: the whole sequence for one chunk of transforms.
+// `nlaunch` (may be NULL) is incremented once per kernel launched.
 template <int V>
-cudaError_t mp_run(const MpArgs& a0, float* W0, float* W1, const SmallConsts& K, cudaStream_t st) {
+cudaError_t mp_run(const MpArgs& a0, float* W0, float* W1, const SmallConsts& K, cudaStream_t st,
+                   long long* nlaunch) {
   MpArgs a = a0;
+  auto launched = [&]() {
+    if (nlaunch) ++*nlaunch;
+    return cudaGetLastError();
+  };
   const int logN = a.logN, N = 1 << logN;
   const int threads = 256;
   auto grid_for = [&](long long items) {
@@ -398,7 +404,7 @@ cudaError_t mp_run(const MpArgs& a0, float* W0, float* W1, const SmallConsts& K,
   float* oth = W1;
   const long long words = a.RSg * 4 * a.nt;
   mp_load_kernel<V><<<grid_for(a.nt * (N / 4)), threads, 0, st>>>(a, cur);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launched()) != cudaSuccess) return e;
   const int smem = mp_solve_smem_bytes();
   e = cudaFuncSetAttribute(mp_solve_kernel<V, MP_TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
@@ -418,53 +424,53 @@ cudaError_t mp_run(const MpArgs& a0, float* W0, float* W1, const SmallConsts& K,
       case 9: mp_fold_band_kernel<V, true, 4><<<grid, threads, 0, st>>>(a, cur, bp.logL[b]); break;
       default: mp_fold_band_kernel<V, false, 4><<<grid, threads, 0, st>>>(a, cur, bp.logL[b]); break;
     }
-    return cudaGetLastError();
+    return launched();
   };
   if constexpr (Var<V>::ot) {
     for (int b = 0; b < bp.nb; ++b)
       if ((e = fold(b, true)) != cudaSuccess) return e;
     mp_solve_kernel<V, MP_TPB><<<nsolve, MP_TPB, smem, st>>>(a, cur, K);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launched()) != cudaSuccess) return e;
     // frequency phase of M4 / M8, one level per pass in gather form (a band
     // would read its descendants bit-reversed, scattered across sectors)
     for (int lp = MP_LOG_S + 1; lp <= logN - 2; ++lp) {
       mp_neighbour_kernel<V><<<grid_for(words), threads, 0, st>>>(a, cur, oth, lp);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = launched()) != cudaSuccess) return e;
       float* t = cur; cur = oth; oth = t;
     }
     for (int lm = MP_LOG_S + 3; lm <= logN - 1; ++lm) {
       mp_chain_kernel<V><<<grid_for(words), threads, 0, st>>>(a, cur, oth, lm);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = launched()) != cudaSuccess) return e;
       float* t = cur; cur = oth; oth = t;
     }
   } else {
     for (int lm = logN - 1; lm >= MP_LOG_S + 3; --lm) {
       mp_chain_kernel<V><<<grid_for(words), threads, 0, st>>>(a, cur, oth, lm);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = launched()) != cudaSuccess) return e;
       float* t = cur; cur = oth; oth = t;
     }
     for (int lp = logN - 2; lp >= MP_LOG_S + 1; --lp) {
       mp_neighbour_kernel<V><<<grid_for(words), threads, 0, st>>>(a, cur, oth, lp);
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = launched()) != cudaSuccess) return e;
       float* t = cur; cur = oth; oth = t;
     }
     mp_solve_kernel<V, MP_TPB><<<nsolve, MP_TPB, smem, st>>>(a, cur, K);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if ((e = launched()) != cudaSuccess) return e;
     for (int b = bp.nb - 1; b >= 0; --b)
       if ((e = fold(b, false)) != cudaSuccess) return e;
   }
   if (a.dtype == 0) {
     mp_store_kernel<V><<<grid_for(a.nt * (N / 4)), threads, 0, st>>>(a, cur);
-    return cudaGetLastError();
+    return launched();
   }
   // 16-bit: the free ping-pong buffer holds the per-transform maxima
   int* Mx = reinterpret_cast<int*>(oth);
   mp_zero_kernel<V><<<(unsigned)((a.nt + 255) / 256), 256, 0, st>>>(Mx, a.nt);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launched()) != cudaSuccess) return e;
   mp_max_kernel<V><<<grid_for(a.nt * (N / 4)), threads, 0, st>>>(a, cur, Mx);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if ((e = launched()) != cudaSuccess) return e;
   mp_store16_kernel<V><<<grid_for(a.nt * (N / 4)), threads, 0, st>>>(a, cur, Mx);
-  return cudaGetLastError();
+  return launched();
 }
 
 }  // namespace amqft

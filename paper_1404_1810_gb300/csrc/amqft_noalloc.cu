@@ -58,12 +58,12 @@ cudaError_t scratch_for(int dev, float** out) {
 }
 
 cudaError_t multipass_dispatch(int variant, const MpArgs& a, float* W0, float* W1, const SmallConsts& K,
-                               cudaStream_t st) {
+                               cudaStream_t st, long long* nl) {
   switch (variant) {
-    case 2: return multipass_variant_2(a, W0, W1, K, st);
-    case 4: return multipass_variant_4(a, W0, W1, K, st);
-    case 6: return multipass_variant_6(a, W0, W1, K, st);
-    default: return multipass_variant_8(a, W0, W1, K, st);
+    case 2: return multipass_variant_2(a, W0, W1, K, st, nl);
+    case 4: return multipass_variant_4(a, W0, W1, K, st, nl);
+    case 6: return multipass_variant_6(a, W0, W1, K, st, nl);
+    default: return multipass_variant_8(a, W0, W1, K, st, nl);
   }
 }
 
@@ -127,7 +127,9 @@ extern "C" int amqft_exec_static(amqft_plan_t plan, int64_t batch, const void* i
     a.tlist = nullptr;
     a.toff = nullptr;
     a.ntdev = nullptr;
-    e = multipass_dispatch(pv.variant, a, scratch, scratch + chunk * 4 * RSg, *pv.small, st);
+    long long nl = 0;
+    e = multipass_dispatch(pv.variant, a, scratch, scratch + chunk * 4 * RSg, *pv.small, st, &nl);
+    add_launches(plan, nl);
     if (e != cudaSuccess)
       return set_error(AMQFT_ERR_CUDA, "amqft_exec_static: multi-pass launch: %s", cudaGetErrorString(e));
   }

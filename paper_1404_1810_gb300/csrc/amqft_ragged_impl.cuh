@@ -124,9 +124,10 @@ struct RaggedLaunch {
   int cluster_tot_off[3];
 };
 
+// `nlaunch` (may be NULL) is incremented once per kernel launched.
 template <int V>
 cudaError_t ragged_run(const FusedArgs& a0, const SmallConsts& K, const RaggedArgs& r, const RaggedLaunch& L,
-                       cudaStream_t st) {
+                       cudaStream_t st, long long* nlaunch) {
   cudaError_t e;
   if (r.maxlog >= 1) {
     auto kern = ragged_small_kernel<V>;
@@ -134,22 +135,26 @@ cudaError_t ragged_run(const FusedArgs& a0, const SmallConsts& K, const RaggedAr
     if (e != cudaSuccess) return e;
     kern<<<(unsigned)L.small_grid, SMALL_TPB, L.small_smem, st>>>(a0, K, r);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (nlaunch) ++*nlaunch;
   }
   FusedArgs a = a0;
   if (r.maxlog >= 14) {
     a.tot_off = L.cluster_tot_off[0];
     e = ragged_cluster_launch<V, 14>(a, K, r, L.clusters[0], L.cluster_smem[0], st);
     if (e != cudaSuccess) return e;
+    if (nlaunch) ++*nlaunch;
   }
   if (r.maxlog >= 15) {
     a.tot_off = L.cluster_tot_off[1];
     e = ragged_cluster_launch<V, 15>(a, K, r, L.clusters[1], L.cluster_smem[1], st);
     if (e != cudaSuccess) return e;
+    if (nlaunch) ++*nlaunch;
   }
   if (r.maxlog >= 16) {
     a.tot_off = L.cluster_tot_off[2];
     e = ragged_cluster_launch<V, 16>(a, K, r, L.clusters[2], L.cluster_smem[2], st);
     if (e != cudaSuccess) return e;
+    if (nlaunch) ++*nlaunch;
   }
   return cudaSuccess;
 }

@@ -15,7 +15,7 @@ def rel(a, b) -> float:
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-def north_star_tol(log2n: int) -> float:
+def target_tol(log2n: int) -> float:
     """rel-L2 bound stated for float32: 2e-7 * log2 N."""
     return 2e-7 * max(1, log2n)
 
@@ -24,7 +24,7 @@ def derived_tol(e32: float, log2n: int) -> float:
     """float32 tolerance against the float64 oracle: the stated bound where the
     algorithm itself meets it, otherwise twice the error of the paper's own
     recursion evaluated in float32 (same inputs, sequential order)."""
-    return max(north_star_tol(log2n), 2.0 * e32)
+    return max(target_tol(log2n), 2.0 * e32)
 
 
 def run_gpu(x: np.ndarray, variant: int, inverse: bool = False) -> np.ndarray:

@@ -53,6 +53,9 @@ def test_argument_checks_need_no_gpu(lib):
     assert lib.amqft_destroy(None) == 0
     lib.amqft_exec_fwd.argtypes = [ctypes.c_void_p] * 5
     assert lib.amqft_exec_fwd(None, None, None, None, None) == -8
+    lib.amqft_plan_launches.argtypes = [ctypes.c_void_p]
+    lib.amqft_plan_launches.restype = ctypes.c_int64
+    assert lib.amqft_plan_launches(None) == -8
 
 
 def test_binding_fails_loudly_without_library(tmp_path):

@@ -100,3 +100,46 @@ def test_multipass_chunked_batch(orc):
     p1.close()
     assert torch.equal(y[b - 1], y1[0])
     assert torch.isfinite(y).all()
+
+
+def _mp_launches(log2n, dtype16=False):
+    """Kernels of one multi-pass chunk (time-first variant): load, the fold
+    bands of the levels 2^(n-2) .. 2^14 (at most four levels a band), the
+    in-shared-memory solve, one neighbour pass per level 2^14 .. 2^(n-2), one
+    chain pass per level 2^16 .. 2^(n-1), and the store (16-bit: zero, maximum
+    and scaled store)."""
+    levels = log2n - 15
+    return 1 + (levels + 3) // 4 + 1 + levels + (log2n - 16) + (3 if dtype16 else 1)
+
+
+def test_launch_count():
+    """amqft_plan_launches counts the kernels each exec call launches."""
+    import torch
+
+    from paper_1404_1810_gb300 import AMQFT_CBF16, Plan, RaggedPlan
+
+    for log2n, expect in ((10, 1), (16, 1), (17, _mp_launches(17)), (18, _mp_launches(18))):
+        x = synth.device_normal_complex64(1 << log2n, 2, "cuda")
+        p = Plan(log2n, 4, 2)
+        assert p.launches() == 0
+        y = p.fwd(x)
+        assert p.launches() == expect, log2n
+        p.inv(y)
+        assert p.launches() == 2 * expect, log2n
+        p.close()
+    p = Plan(17, 4, 2, dtype=AMQFT_CBF16)
+    x16 = torch.zeros((2, 1 << 17, 2), dtype=torch.bfloat16, device="cuda")
+    p.fwd(x16)
+    assert p.launches() == _mp_launches(17, dtype16=True)
+    p.close()
+    # ragged: bucket, the persistent small launch, three cluster launches and
+    # the multi-pass sequences of 2^17 and 2^18
+    lg = torch.tensor([4, 10, 14, 15, 16, 17, 18], dtype=torch.uint8, device="cuda")
+    n = (1 << lg.to(torch.int64))
+    off = torch.cumsum(n, 0) - n
+    x = synth.device_normal_complex64(int(n.sum()), 1, "cuda").reshape(-1)
+    rp = RaggedPlan(18, 4, 16, 1 << 20)
+    rp.exec(x, lg, off)
+    torch.cuda.synchronize()
+    assert rp.launches() == 1 + 1 + 3 + _mp_launches(17) + _mp_launches(18)
+    rp.close()

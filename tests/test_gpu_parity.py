@@ -13,7 +13,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_util import (EXACT_VARIANTS, SCAN_VARIANTS, derived_tol, north_star_tol, rel, run_gpu)
+from gpu_util import (EXACT_VARIANTS, SCAN_VARIANTS, derived_tol, target_tol, rel, run_gpu)
 
 pytestmark = pytest.mark.gpu
 VARIANTS = list(range(1, 9))
@@ -92,7 +92,7 @@ def test_roundtrip(v, log2n):
     y = run_gpu(x, v)
     z = run_gpu(y, v, inverse=True)
     # twice the forward error of the float32 recursion (about 1e-5 at 2^16)
-    tol = 3.0 * max(north_star_tol(log2n), 1.2e-5 if log2n >= 14 else 0.0)
+    tol = 3.0 * max(target_tol(log2n), 1.2e-5 if log2n >= 14 else 0.0)
     assert rel(z, n * x) < tol
 
 

@@ -105,7 +105,11 @@ __global__ void mp_max_kernel(MpArgs a, const float* W, int* Mx) {
     const int k = (int)(w & ((1LL << logQ) - 1));
     const Out4 o = emit_values<V>(a.logN, k, store_gather<V>(rg, a.logN, (int)t, k));
     const float m = out4_absmax(o);
-    if (m > 0.f) atomicMax(Mx + t, __float_as_int(m));
+    // a warp's 32 consecutive items belong to one transform (N/4 and the total
+    // are multiples of 32, so the loop is warp-uniform): one atomic per warp.
+    // Positive floats order as their bit patterns; zeros and NaN count as 0.
+    const unsigned mw = __reduce_max_sync(0xffffffffu, m > 0.f ? __float_as_uint(m) : 0u);
+    if ((threadIdx.x & 31) == 0 && mw != 0u) atomicMax(Mx + t, (int)mw);
   }
 }
 

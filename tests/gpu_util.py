@@ -43,3 +43,15 @@ def run_gpu(x: np.ndarray, variant: int, inverse: bool = False) -> np.ndarray:
     finally:
         plan.close()
     return y.cpu().numpy().astype(np.complex128)
+
+
+def expected_exponent(vals32):
+    """Exponent of a 16-bit-stored transform: floor(log2 max|component|) - 13,
+    so that the largest component lands in [2^13, 2^14) once scaled by
+    2^-exponent; clamped to [-100, 100]; 0 for an all-zero or non-finite
+    maximum."""
+    m = float(np.max(np.abs(np.stack([vals32.real, vals32.imag]))))
+    if not (m > 0.0) or not np.isfinite(m):
+        return 0
+    _, E = np.frexp(np.float32(m))
+    return int(min(100, max(-100, max(int(E) - 1, -126) - 13)))

@@ -12,7 +12,7 @@ import numpy as np
 import pytest
 
 import synth
-from gpu_util import rel
+from gpu_util import expected_exponent, rel
 
 pytestmark = pytest.mark.gpu
 
@@ -41,15 +41,6 @@ def quantize_input(x, dt):
     import torch
 
     return torch.view_as_real(torch.from_numpy(np.ascontiguousarray(x))).to(_tdt(dt)).contiguous()
-
-
-def expected_exponent(vals32):
-    """floor(log2 max|component|) - 13, clamped to [-100, 100]; 0 for zero."""
-    m = float(np.max(np.abs(np.stack([vals32.real, vals32.imag]))))
-    if not (m > 0.0) or not np.isfinite(m):
-        return 0
-    _, E = np.frexp(np.float32(m))
-    return int(min(100, max(-100, max(int(E) - 1, -126) - 13)))
 
 
 def run16(x16, log2n, v, dt, inverse=False, exp_in=None):

@@ -50,3 +50,27 @@ def test_no_cpu_fallback():
     build.build()
     with pytest.raises(AmqftError):
         Plan(10, 4, 1)                  # no CUDA device: the plan cannot be made
+
+
+def test_expected_exponent_puts_the_maximum_in_range():
+    """16-bit storage reading: the exponent is the one power of two that scales
+    the largest component magnitude into [2^13, 2^14), clamped to [-100, 100],
+    and 0 for an all-zero or non-finite transform.  Checked against a direct
+    search over exponents, not against the helper's own formula."""
+    from gpu_util import expected_exponent
+
+    rng = np.random.default_rng(14041810)
+    for _ in range(2000):
+        mag = np.float32(10.0 ** rng.uniform(-25, 30))
+        v = (rng.standard_normal(16) + 1j * rng.standard_normal(16)).astype(np.complex64)
+        v = (v / np.max(np.abs(np.stack([v.real, v.imag]))) * mag).astype(np.complex64)
+        m = float(np.max(np.abs(np.stack([v.real, v.imag]))))
+        want = next(e for e in range(-200, 200) if 2.0 ** 13 <= m * 2.0 ** -e < 2.0 ** 14)
+        assert expected_exponent(v) == min(100, max(-100, want))
+    # boundaries: exactly 2^13 and just below 2^14 keep exponent 0
+    assert expected_exponent(np.array([2.0 ** 13], np.complex64)) == 0
+    assert expected_exponent(np.array([np.nextafter(np.float32(2.0 ** 14), np.float32(0))], np.complex64)) == 0
+    assert expected_exponent(np.array([2.0 ** 14], np.complex64)) == 1
+    assert expected_exponent(np.array([1j * -3.0 * 2.0 ** 20], np.complex64)) == 8
+    assert expected_exponent(np.zeros(4, np.complex64)) == 0
+    assert expected_exponent(np.array([np.inf, 1.0], np.complex64)) == 0

@@ -67,7 +67,10 @@ typedef struct amqft_plan_s *amqft_plan_t;
  * read and write per sample).  Longer transforms (variants 2, 4, 6, 8 only:
  * the others contain recurrences) run as several passes over a workspace the
  * plan allocates: two buffers of the transform's size per transform of a
- * chunk, at most 2 GiB, the batch processed chunk by chunk.
+ * chunk, at most 2 GiB, the batch processed chunk by chunk.  That workspace
+ * (like the staging of amqft_exec_host) belongs to the plan, so the exec calls
+ * of one plan must be ordered: one stream, or streams joined by events.  Calls
+ * on different plans are independent.
  * Errors: AMQFT_ERR_N (log2n < 0 or > AMQFT_LOG2N_MAX), AMQFT_ERR_VARIANT
  * (also variants 1, 3, 5, 7 with log2n > AMQFT_LOG2N_FUSED_MAX),
  * AMQFT_ERR_DTYPE (not an amqft_dtype), AMQFT_ERR_ARG (out NULL or batch < 0), AMQFT_ERR_DEVICE,

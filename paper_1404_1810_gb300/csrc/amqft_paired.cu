@@ -1,0 +1,21 @@
+// Dispatch of the paired-region kernel (amqft_paired.cuh): batched complex64
+// transforms of 2^14 .. 2^16 points, variant 4.
+#include "amqft_internal.h"
+
+namespace amqft {
+
+bool paired_supported(int logN, int variant, int dtype) {
+  return variant == 4 && dtype == AMQFT_C64 && logN >= 14 && logN <= 16;
+}
+
+cudaError_t paired_launch(int logN, const void* in, void* out, long long batch, int inverse, const float* ctab,
+                          const SmallConsts& K, cudaStream_t st) {
+  switch (logN) {
+    case 14: return paired_launch_14(in, out, batch, inverse, ctab, K, st);
+    case 15: return paired_launch_15(in, out, batch, inverse, ctab, K, st);
+    case 16: return paired_launch_16(in, out, batch, inverse, ctab, K, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace amqft

@@ -1,0 +1,795 @@
+// Paired-region AM-QFT kernel ("A class of AM-QFT algorithms for power-of-two
+// FFT", Pasquini): one complex transform of N = 2^LN (LN = 14..16) per cluster
+// of four CTAs, time-first variant 4 (Sect. 6.9: D_n chain, D_k trees, M4
+// conversion of Tab. 5-6), persistent over the batch.
+//
+// The pairing.  D_c (Sect. 3.1) and D_r (Eq. qft_22-23) turn x = a + ib into
+// the DCT-0 and DST-0 inputs of a and b.  The DCT of a and the DCT of b run
+// exactly the same operations (the same holds for the two DSTs), so they
+// travel as one float2 (value of a, value of b) and every butterfly is one
+// sm_100+ f32x2 instruction (add / sub / mul .rn.f32x2: two IEEE float32
+// operations, so the results are those of the scalar recursion).  The loaded
+// pair x(n) +- x(N-n) is already that float2: D_c and D_r together cost one
+// f32x2 add and one f32x2 sub per sample pair.
+//
+// The split.  With Q = N/4 = 2^T, the DCT region holds the dct_ot(N) tree of
+// Q values (odd samples) followed by the rest of the D_n chain (Q + 1
+// values); the DST region likewise (Q and Q - 1).  Cluster rank r:
+//     0: DCT tree 0    1: DCT rest    2: DST tree 0    3: DST rest
+// so every CTA holds 2^T float2 in shared memory (one CTA per SM at 2^16).
+//
+// The schedule inside a CTA (NT = 2^(T-5) threads, 32 float2 each; a warp
+// owns one block of 1024 positions):
+//   load     HBM -> pairs -> distributed shared memory (all four CTAs).
+//   band A   the top T-10 time levels of the trees, CTA-wide: every thread
+//            holds a fold orbit (the positions closed under the D_k
+//            reflections of those levels) and works in registers.
+//   warp     per 1024-block, warp-synchronous: five time levels (fold
+//            orbit), the 32-value register leaves (the recursion itself), five
+//            frequency levels (each lane holds element lane of the 32 leaves
+//            and climbs in registers; the M4 neighbour of the last element of
+//            a lane's chunk is read from shared memory: along the A path it
+//            is an input value).
+//   F-band   the top T-10 frequency levels, CTA-wide, the same way.
+//   chain    rest CTAs: the D_n frequency phase (S(k) = E(k) +- O(k)) of the
+//            chain levels below N, in place, four outputs per quad.
+//   store    the last chain level, D_r^F (Eq. qft_24-25) and D_c^F (Eq.
+//            qft_17-21), reading the four CTAs through distributed shared
+//            memory, float4 stores to HBM.
+// The rest CTAs' trees 1, 2, ... and the chain remainder are handled by the
+// same band code with a compile-time "virtual root" rule: at every level the
+// last aligned block is not a tree node (it is the chain), and its values are
+// left alone.  The last warp's block holds the trees below 1024 values and
+// the chain bottom (one lane runs the base cases and the chain up to dct(64)).
+//
+// Layout: every tree node stores its time data and its spectrum in natural
+// order; the children of a node of size L occupy [0, L/2) (A: the e-child of
+// D_k) and [L/2, L) (B: the oo child after M_v).  A position p is stored at
+// float2 index p + 2 (p >> 5) (two pad slots per 32, so that both a lane-per-
+// position and a lane-per-32-run access pattern are free of bank conflicts).
+// A band reads all its values, synchronises its threads, then writes.
+//
+// The device code is written so that it also compiles for the host: the
+// stages take the thread index and shared-memory pointers explicitly.
+#pragma once
+
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#define PR_HD __host__ __device__ __forceinline__
+#else
+#define PR_HD inline
+#endif
+
+namespace amqft {
+namespace pr {
+
+// ---------------------------------------------------------------------
+// f32x2 arithmetic (round to nearest, never contracted)
+// ---------------------------------------------------------------------
+// The operations are written as PTX with an explicit rounding mode: such an
+// instruction is never contracted with a neighbouring multiply into an FMA.
+#if defined(__CUDA_ARCH__)
+#define AMQFT_F32X2(OP, r, a, b)                                                                \
+  asm("{\n\t.reg .b64 u, v, w;\n\tmov.b64 u, {%2, %3};\n\tmov.b64 v, {%4, %5};\n\t" OP \
+      " w, u, v;\n\tmov.b64 {%0, %1}, w;\n\t}"                                              \
+      : "=f"(r.x), "=f"(r.y)                                                                   \
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y))
+#endif
+
+PR_HD float2 add2(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__)
+  float2 r;
+  AMQFT_F32X2("add.rn.f32x2", r, a, b);
+  return r;
+#else
+  return make_float2(a.x + b.x, a.y + b.y);
+#endif
+}
+
+PR_HD float2 sub2(float2 a, float2 b) {
+#if defined(__CUDA_ARCH__)
+  float2 r;
+  AMQFT_F32X2("sub.rn.f32x2", r, a, b);
+  return r;
+#else
+  return make_float2(a.x - b.x, a.y - b.y);
+#endif
+}
+
+// Product a * c, rounded once.  ptxas contracts an f32x2 multiply into the
+// f32x2 add that consumes it even when both carry .rn, so the product is
+// formed as fma(a, c, nz) with nz = -0.0 passed in at run time (a * c + (-0)
+// is the rounded product, signed zeros included): an FMA with an unknown
+// addend cannot be fused into anything else.
+PR_HD float2 mul2(float2 a, float c, float nz) {
+#if defined(__CUDA_ARCH__)
+  float2 r;
+  asm("{\n\t.reg .b64 u, v, z, w;\n\tmov.b64 u, {%2, %3};\n\tmov.b64 v, {%4, %4};\n\t"
+      "mov.b64 z, {%5, %5};\n\tfma.rn.f32x2 w, u, v, z;\n\tmov.b64 {%0, %1}, w;\n\t}"
+      : "=f"(r.x), "=f"(r.y)
+      : "f"(a.x), "f"(a.y), "f"(c), "f"(nz));
+  return r;
+#else
+  (void)nz;
+  return make_float2(a.x * c, a.y * c);
+#endif
+}
+
+// physical float2 index of region position p (two pad slots per 32)
+PR_HD constexpr int phys(int p) { return p + ((p >> 5) << 1); }
+
+// D_k time phase of one pair (Tab. 4) and the M4 scaling of its oo value
+// (Tab. 5): DCT context A = u + w, B = (u - w) c; DST context A = u - w,
+// B = (u + w) c, with c = 1 / (2 cos(2 pi (2i+1) / 4L)) for the pair
+// (i, L-1-i) of a node of L values.
+template <int CX>
+PR_HD void bfly(float2 u, float2 w, float c, float nz, float2& A, float2& B) {
+  if constexpr (CX == 0) {
+    A = add2(u, w);
+    B = mul2(sub2(u, w), c, nz);
+  } else {
+    A = sub2(u, w);
+    B = mul2(add2(u, w), c, nz);
+  }
+}
+
+// Constants of the leaf levels (node sizes 2..32), from the plan's table:
+// node size L holds its L/2 constants at [L/2 - 2, L - 2).
+struct LeafConsts {
+  float c[30];
+  float cos_pi4;  // node size 2 (the oo(8) base case, Sect. 7.1)
+  float nz;       // -0.0, the addend of every product (see mul2)
+};
+
+// ---------------------------------------------------------------------
+// register recursion: dct_ot(4L) (CX 0) / dst_ot(4L) (CX 1) on L values,
+// time values in natural order in, spectrum in natural order out
+// ---------------------------------------------------------------------
+template <int L, int CX>
+PR_HD void ot2(float2 (&x)[L], const LeafConsts& K) {
+  if constexpr (L >= 2) {
+    constexpr int H = L / 2;
+    float2 a[H], b[H];
+#pragma unroll
+    for (int i = 0; i < H; ++i) bfly<CX>(x[i], x[L - 1 - i], L == 2 ? K.cos_pi4 : K.c[H - 2 + i], K.nz, a[i], b[i]);
+    ot2<H, CX>(a, K);
+    ot2<H, CX>(b, K);
+    // M4 frequency phase: DCT o[j] = B[j] + B[j+1], o[H-1] = B[H-1];
+    // DST o[0] = B[0], o[j] = B[j-1] + B[j]; then D_k^F interleaves.
+    if constexpr (CX == 0) {
+#pragma unroll
+      for (int j = 0; j < H; ++j) {
+        x[2 * j] = a[j];
+        x[2 * j + 1] = (j + 1 < H) ? add2(b[j], b[j + 1]) : b[j];
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < H; ++j) {
+        x[2 * j] = (j > 0) ? add2(b[j - 1], b[j]) : b[j];
+        x[2 * j + 1] = a[j];
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------
+// vector access of R consecutive positions p .. p+R-1 (p a multiple of R,
+// R <= 32): one run inside a 32-group, contiguous in shared memory
+// ---------------------------------------------------------------------
+template <int R>
+PR_HD void ld_run(const float2* __restrict__ sm, int p, float2* v) {
+  const float2* s = sm + phys(p);
+  if constexpr (R == 1) {
+    v[0] = s[0];
+  } else {
+#pragma unroll
+    for (int e = 0; e < R; e += 2) {
+      const float4 q = *reinterpret_cast<const float4*>(s + e);
+      v[e] = make_float2(q.x, q.y);
+      v[e + 1] = make_float2(q.z, q.w);
+    }
+  }
+}
+
+template <int R>
+PR_HD void st_run(float2* __restrict__ sm, int p, const float2* v) {
+  float2* s = sm + phys(p);
+  if constexpr (R == 1) {
+    s[0] = v[0];
+  } else {
+#pragma unroll
+    for (int e = 0; e < R; e += 2) *reinterpret_cast<float4*>(s + e) = make_float4(v[e].x, v[e].y, v[e + 1].x, v[e + 1].y);
+  }
+}
+
+// ---------------------------------------------------------------------
+// fold band: S time levels of the D_k trees below one band root of 2^M
+// positions.  Thread b of 2^(M-S-RHO) holds the 32 labels (f, h, e):
+//   position f 2^B0 + (h ? 2^B0 - 1 - (b R0 + e) : b R0 + e),  B0 = M - S + 1,
+// f < 2^(S-1), h in {0,1}, e < R0 = 2^RHO: the orbit of its positions under
+// the reflections i <-> L-1-i of every level from 2^M down to 2^B0.
+// VIRT: the band root is not a tree node and at every level the last aligned
+// node is not one either (it is the D_n chain): those values are left alone.
+// After the band, label (f, h, e) is element b R0 + e of sub-node 2f + h
+// (children of size 2^(B0-1)).
+// ---------------------------------------------------------------------
+template <int M, int S, int RHO>
+struct Fold {
+  static constexpr int B0 = M - S + 1, R0 = 1 << RHO, NF = 1 << (S - 1), NV = NF * 2 * R0;
+  static constexpr int NTH = 1 << (B0 - 1 - RHO);
+  PR_HD static constexpr int idx(int f, int h, int e) { return (f * 2 + h) * R0 + e; }
+};
+
+// does the last sub-node of size 2^B0 (f = NF-1) take part (not for VIRT)
+template <bool VIRT, int NF>
+PR_HD constexpr bool fold_f_used(int f) {
+  return !(VIRT && f == NF - 1);
+}
+
+template <int M, int S, int RHO, bool VIRT>
+PR_HD void fold_read(const float2* __restrict__ sm, int root, int b, float2 (&x)[Fold<M, S, RHO>::NV]) {
+  using G = Fold<M, S, RHO>;
+  constexpr int U = 1 << G::B0;
+#pragma unroll
+  for (int f = 0; f < G::NF; ++f) {
+    if (!fold_f_used<VIRT, G::NF>(f)) continue;
+    float2 v[G::R0];
+    ld_run<G::R0>(sm, root + f * U + b * G::R0, v);
+#pragma unroll
+    for (int e = 0; e < G::R0; ++e) x[G::idx(f, 0, e)] = v[e];
+    ld_run<G::R0>(sm, root + f * U + U - (b + 1) * G::R0, v);
+#pragma unroll
+    for (int e = 0; e < G::R0; ++e) x[G::idx(f, 1, e)] = v[G::R0 - 1 - e];
+  }
+}
+
+// one level m of the fold band (compile-time recursion over the levels)
+template <int M, int S, int RHO, int CX, bool VIRT, int m>
+PR_HD void fold_level(float2 (&x)[Fold<M, S, RHO>::NV], const float* __restrict__ cst, int b, float nz) {
+  using G = Fold<M, S, RHO>;
+  constexpr int FB = m - G::B0;      // f bits local to a node of size 2^m
+  constexpr int NN = 1 << (M - m);   // nodes of size 2^m under the band root
+  constexpr int L = 1 << m;
+  constexpr int U = 1 << G::B0;
+  // constants of node size L at cst[L/2 - 32 + i] (the table starts at L = 64)
+  const float* c0 = cst + (L / 2 - 32) + b * G::R0;
+  const float* c1 = cst + (L / 2 - 32) + (U - 1) - b * G::R0;
+  float2 y[G::NV];
+#pragma unroll
+  for (int q = 0; q < G::NV; ++q) y[q] = x[q];
+#pragma unroll
+  for (int f = 0; f < G::NF; ++f) {
+    const int nid = f >> FB;
+    if (VIRT && nid == NN - 1) continue;
+    if constexpr (FB >= 1) {
+      const int fl = f & ((1 << FB) - 1);
+      if (fl >= (1 << (FB - 1))) continue;
+      const int fh = (f & ~((1 << FB) - 1)) | ((1 << FB) - 1 - fl);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+#pragma unroll
+        for (int e = 0; e < G::R0; ++e) {
+          const float c = h == 0 ? c0[fl * U + e] : c1[fl * U - e];
+          float2 A, B;
+          bfly<CX>(x[G::idx(f, h, e)], x[G::idx(fh, 1 - h, e)], c, nz, A, B);
+          y[G::idx(f, h, e)] = A;
+          y[G::idx(f + (1 << (FB - 1)), h, e)] = B;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int e = 0; e < G::R0; ++e) {
+        float2 A, B;
+        bfly<CX>(x[G::idx(f, 0, e)], x[G::idx(f, 1, e)], c0[e], nz, A, B);
+        y[G::idx(f, 0, e)] = A;
+        y[G::idx(f, 1, e)] = B;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < G::NV; ++q) x[q] = y[q];
+  if constexpr (m > G::B0) fold_level<M, S, RHO, CX, VIRT, m - 1>(x, cst, b, nz);
+}
+
+template <int M, int S, int RHO, int CX, bool VIRT>
+PR_HD void fold_compute(float2 (&x)[Fold<M, S, RHO>::NV], const float* __restrict__ cst, int b, float nz) {
+  if constexpr (VIRT) {
+    if constexpr (M - 1 >= Fold<M, S, RHO>::B0) fold_level<M, S, RHO, CX, VIRT, M - 1>(x, cst, b, nz);
+  } else {
+    fold_level<M, S, RHO, CX, VIRT, M>(x, cst, b, nz);
+  }
+}
+
+template <int M, int S, int RHO, bool VIRT>
+PR_HD void fold_write(float2* __restrict__ sm, int root, int b, const float2 (&x)[Fold<M, S, RHO>::NV]) {
+  using G = Fold<M, S, RHO>;
+  constexpr int HU = 1 << (G::B0 - 1);
+#pragma unroll
+  for (int f = 0; f < G::NF; ++f) {
+    if (!fold_f_used<VIRT, G::NF>(f)) continue;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) st_run<G::R0>(sm, root + (2 * f + h) * HU + b * G::R0, &x[G::idx(f, h, 0)]);
+  }
+}
+
+// ---------------------------------------------------------------------
+// frequency band: S frequency levels above G = 2^S sibling nodes of 2^M0
+// positions.  Thread c of NC = 2^(M0-RHO) holds chunk c (R0 = 2^RHO values)
+// of every sibling; a level turns chunk c of children A = 2g and B = 2g+1 into
+// chunk c (twice the size) of their parent:
+//   DCT: P[2i] = A[i], P[2i+1] = B[i] + B[i+1]   (B[L/2] absent)
+//   DST: P[2i] = B[i-1] + B[i], P[2i+1] = A[i]   (B[-1] absent)
+// (M4 frequency phase and D_k^F, Tab. 4-5).  The neighbour outside the chunk
+// is the first (DCT) / last (DST) element of the next / previous thread's
+// chunk of B; B's even (DCT) / odd (DST) elements are its A child's, so that
+// value is an input of the band: input node (2g+1) 2^(j-1), element
+// (c+1) R0 (DCT) or c R0 - 1 (DST).
+// VIRT: at every level the last node is not formed (chain); the first child
+// of each such node is a finished tree root and is written out.
+// ---------------------------------------------------------------------
+template <int M0, int S, int RHO>
+struct Freq {
+  static constexpr int G = 1 << S, R0 = 1 << RHO, NV = G * R0, NC = 1 << (M0 - RHO);
+};
+
+
+// node gp of level j is formed (VIRT: all but the last)
+template <bool VIRT, int G, int j>
+PR_HD constexpr bool freq_formed(int gp) {
+  return VIRT ? gp < (G >> j) - 1 : true;
+}
+
+// inputs: chunk c of every sibling (VIRT: not the last two; the next to last
+// is a finished tree root, the last the chain)
+template <int M0, int S, int RHO, bool VIRT>
+PR_HD void freq_read(const float2* __restrict__ sm, int base, int c, float2 (&v)[Freq<M0, S, RHO>::NV]) {
+  using F = Freq<M0, S, RHO>;
+#pragma unroll
+  for (int g = 0; g < F::G; ++g)
+    if (!VIRT || g < F::G - 2) ld_run<F::R0>(sm, base + (g << M0) + c * F::R0, &v[g * F::R0]);
+}
+
+// v holds, at level j, chunk c (R0 2^j values) of node g of that level in
+// slots [g R0 2^j, (g+1) R0 2^j): a node always occupies its descendants'
+// slots, so a level rewrites the slots of its formed nodes in place, and a
+// tree root finished below a node that is not formed (VIRT) stays put.
+template <int M0, int S, int RHO, int CX, bool VIRT, int j>
+PR_HD void freq_level(float2 (&v)[Freq<M0, S, RHO>::NV], const float2* __restrict__ sm, int base, int el,
+                      bool has) {
+  using F = Freq<M0, S, RHO>;
+  constexpr int Rc = F::R0 << (j - 1);
+#pragma unroll
+  for (int gp = 0; gp < (F::G >> j); ++gp) {
+    if (!freq_formed<VIRT, F::G, j>(gp)) continue;
+    float2 h = make_float2(0.f, 0.f);
+    if (has) h = sm[phys(base + (((2 * gp + 1) << (j - 1)) << M0) + el)];
+    float2 P[2 * Rc];
+    const int a0 = (2 * gp) * Rc, b0 = (2 * gp + 1) * Rc;
+    if constexpr (CX == 0) {
+#pragma unroll
+      for (int i = 0; i < Rc; ++i) {
+        P[2 * i] = v[a0 + i];
+        if (i + 1 < Rc) P[2 * i + 1] = add2(v[b0 + i], v[b0 + i + 1]);
+        else P[2 * i + 1] = has ? add2(v[b0 + i], h) : v[b0 + i];
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < Rc; ++i) {
+        if (i > 0) P[2 * i] = add2(v[b0 + i - 1], v[b0 + i]);
+        else P[2 * i] = has ? add2(h, v[b0]) : v[b0];
+        P[2 * i + 1] = v[a0 + i];
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < 2 * Rc; ++i) v[a0 + i] = P[i];
+  }
+  if constexpr (j < S) freq_level<M0, S, RHO, CX, VIRT, j + 1>(v, sm, base, el, has);
+}
+
+// the levels of the band; the neighbour of a chunk's edge (its halo) is read
+// here, before the band's writes
+template <int M0, int S, int RHO, int CX, bool VIRT>
+PR_HD void freq_compute(float2 (&v)[Freq<M0, S, RHO>::NV], const float2* __restrict__ sm, int base, int c) {
+  using F = Freq<M0, S, RHO>;
+  const bool has = CX == 0 ? (c + 1 < F::NC) : (c > 0);
+  const int el = CX == 0 ? (c + 1) * F::R0 : c * F::R0 - 1;
+  freq_level<M0, S, RHO, CX, VIRT, 1>(v, sm, base, el, has);
+}
+
+// outputs: chunk c of the band top (VIRT: of the tree roots finished at
+// levels 1 .. S-1, node (G >> l) - 2 of level l)
+template <int M0, int S, int RHO, bool VIRT, int l>
+PR_HD void freq_write_roots(float2* __restrict__ sm, int base, int c, const float2 (&v)[Freq<M0, S, RHO>::NV]) {
+  using F = Freq<M0, S, RHO>;
+  constexpr int Rl = F::R0 << l, gp = (F::G >> l) - 2;
+  st_run<Rl>(sm, base + (gp << (M0 + l)) + c * Rl, &v[gp * Rl]);
+  if constexpr (l + 1 < S) freq_write_roots<M0, S, RHO, VIRT, l + 1>(sm, base, c, v);
+}
+
+template <int M0, int S, int RHO, bool VIRT>
+PR_HD void freq_write(float2* __restrict__ sm, int base, int c, const float2 (&v)[Freq<M0, S, RHO>::NV]) {
+  using F = Freq<M0, S, RHO>;
+  if constexpr (!VIRT) {
+    st_run<F::NV>(sm, base + c * F::NV, v);
+  } else if constexpr (S >= 2) {
+    freq_write_roots<M0, S, RHO, VIRT, 1>(sm, base, c, v);
+  }
+}
+
+// ---------------------------------------------------------------------
+// chain bottom, one thread: the trees of 16 .. 1 values (DCT) or 16 .. 2
+// (DST), the base case dct(2) or dst(4), and the D_n frequency phase up to
+// dct(64) / dst(64), on the 33 (DCT) or 31 (DST) positions [992, 1025) of
+// the last block.  Chain level of periodisation M (Sect. 6.9):
+//   DCT  S(k) = E(k) + O(k), S(M/2-k) = E(k) - O(k) (k < M/4), S(M/4) = E(M/4)
+//   DST  S(k) = O(k) + E(k), S(M/2-k) = O(k) - E(k) (0 < k < M/4), S(M/4) = O(M/4)
+// with O the dct_ot(M) / dst_ot(M) tree and E = dct(M/2) / dst(M/2).
+// ---------------------------------------------------------------------
+template <int OFF, int L, int CX, int SZ>
+PR_HD void tail_tree(float2 (&t)[SZ], const LeafConsts& K) {
+  float2 x[L];
+#pragma unroll
+  for (int e = 0; e < L; ++e) x[e] = t[OFF + e];
+  ot2<L, CX>(x, K);
+#pragma unroll
+  for (int e = 0; e < L; ++e) t[OFF + e] = x[e];
+}
+
+template <int M, int SZ>
+PR_HD void tail_chain_dct(float2 (&t)[SZ]) {
+  if constexpr (M <= 64) {
+    constexpr int P = 32 - M / 2, Q = M / 4;
+    float2 s[M / 2 + 1];
+#pragma unroll
+    for (int k = 0; k < Q; ++k) {
+      s[k] = add2(t[P + Q + k], t[P + k]);
+      s[M / 2 - k] = sub2(t[P + Q + k], t[P + k]);
+    }
+    s[Q] = t[P + 2 * Q];
+#pragma unroll
+    for (int k = 0; k <= M / 2; ++k) t[P + k] = s[k];
+    tail_chain_dct<2 * M, SZ>(t);
+  }
+}
+
+template <int M, int SZ>
+PR_HD void tail_chain_dst(float2 (&t)[SZ]) {
+  if constexpr (M <= 64) {
+    constexpr int P = 32 - M / 2, Q = M / 4;
+    float2 s[M / 2 - 1];
+#pragma unroll
+    for (int k = 1; k < Q; ++k) {
+      s[k - 1] = add2(t[P + k - 1], t[P + Q + k - 1]);
+      s[M / 2 - k - 1] = sub2(t[P + k - 1], t[P + Q + k - 1]);
+    }
+    s[Q - 1] = t[P + Q - 1];
+#pragma unroll
+    for (int k = 0; k < M / 2 - 1; ++k) t[P + k] = s[k];
+    tail_chain_dst<2 * M, SZ>(t);
+  }
+}
+
+// blk: the block's base (float2 index of its position 0)
+template <int CX>
+PR_HD void run_tail(float2* __restrict__ blk, const LeafConsts& K) {
+  constexpr int SZ = CX == 0 ? 33 : 31;
+  float2 t[SZ];
+#pragma unroll
+  for (int e = 0; e < SZ; ++e) t[e] = blk[phys(992 + e)];
+  tail_tree<0, 16, CX, SZ>(t, K);
+  tail_tree<16, 8, CX, SZ>(t, K);
+  tail_tree<24, 4, CX, SZ>(t, K);
+  tail_tree<28, 2, CX, SZ>(t, K);
+  if constexpr (CX == 0) {
+    // dct_ot(4) of one value is a copy; dct(2): S0 = s0 + s1, S1 = s0 - s1
+    const float2 a = t[31], b = t[32];
+    t[31] = add2(a, b);
+    t[32] = sub2(a, b);
+    tail_chain_dct<4, SZ>(t);
+  } else {
+    tail_chain_dst<8, SZ>(t);  // dst(4): S(1) = s(1), a copy
+  }
+#pragma unroll
+  for (int e = 0; e < SZ; ++e) blk[phys(992 + e)] = t[e];
+}
+
+// ---------------------------------------------------------------------
+// one chain level, in place: the tree of 2^m values at [P, P + 2^m) and the
+// chain below at [P + 2^m, ...), P = top - 2^(m+1) (top: the chain's end,
+// position N/4 of the rest region, or 1024 of the last block); item k covers
+// S at k, 2^(m+1) - k, 2^m - k, 2^m + k.  Items k0, k0 + step, ...
+// ---------------------------------------------------------------------
+template <int CX>
+PR_HD void chain_level(float2* __restrict__ sm, int P, int m, int k0, int step) {
+  const int H = 1 << m;
+  if (CX == 0) {
+    for (int k = k0; k <= H / 2; k += step) {
+      if (k == 0) {
+        const float2 o = sm[phys(P)], e = sm[phys(P + H)], eH = sm[phys(P + 2 * H)];
+        sm[phys(P)] = add2(e, o);
+        sm[phys(P + 2 * H)] = sub2(e, o);
+        sm[phys(P + H)] = eH;
+      } else if (k == H / 2) {
+        const float2 o = sm[phys(P + k)], e = sm[phys(P + H + k)];
+        sm[phys(P + k)] = add2(e, o);
+        sm[phys(P + 2 * H - k)] = sub2(e, o);
+      } else {
+        const float2 o1 = sm[phys(P + k)], e1 = sm[phys(P + H + k)];
+        const float2 o2 = sm[phys(P + H - k)], e2 = sm[phys(P + 2 * H - k)];
+        sm[phys(P + k)] = add2(e1, o1);
+        sm[phys(P + 2 * H - k)] = sub2(e1, o1);
+        sm[phys(P + H - k)] = add2(e2, o2);
+        sm[phys(P + H + k)] = sub2(e2, o2);
+      }
+    }
+  } else {
+    for (int k = k0 + 1; k <= H / 2; k += step) {
+      if (k == H / 2) {
+        const float2 o = sm[phys(P + k - 1)], e = sm[phys(P + H + k - 1)];
+        sm[phys(P + k - 1)] = add2(o, e);
+        sm[phys(P + 2 * H - k - 1)] = sub2(o, e);
+      } else {
+        const float2 o1 = sm[phys(P + k - 1)], e1 = sm[phys(P + H + k - 1)];
+        const float2 o2 = sm[phys(P + H - k - 1)], e2 = sm[phys(P + 2 * H - k - 1)];
+        sm[phys(P + k - 1)] = add2(o1, e1);
+        sm[phys(P + 2 * H - k - 1)] = sub2(o1, e1);
+        sm[phys(P + H - k - 1)] = add2(o2, e2);
+        sm[phys(P + H + k - 1)] = sub2(o2, e2);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------
+// stage entry points (thread index explicit; the caller synchronises
+// between the phases marked "sync")
+// ---------------------------------------------------------------------
+// Band A over the CTA's 2^T positions: fold band M = T, S = T - 10 levels,
+// chunk 2^(15-T); VIRT for the rest CTAs (trees 1, 2, ... below a root that
+// is not a node).
+template <int T>
+struct BandA {
+  static constexpr int M = T, S = T - 10, RHO = 15 - T;
+  using G = Fold<M, S, RHO>;
+};
+
+// leaf ln of the block (VIRT: lane 31 runs the chain bottom instead)
+template <int CX, bool VIRT>
+PR_HD void block_leaf(float2* __restrict__ blk, int ln, const LeafConsts& K) {
+  if (VIRT && ln == 31) {
+    run_tail<CX>(blk, K);
+    return;
+  }
+  float2 x[32];
+  ld_run<32>(blk, 32 * ln, x);
+  ot2<32, CX>(x, K);
+  st_run<32>(blk, 32 * ln, x);
+}
+
+// chain levels 5 .. MTOP inside the last block (lanes of one warp, warp
+// synchronisation between levels is the caller's: this runs one level)
+template <int CX>
+PR_HD void block_chain_level(float2* __restrict__ blk, int m, int ln) {
+  chain_level<CX>(blk, 1024 - (2 << m), m, ln, 32);
+}
+
+// ---------------------------------------------------------------------
+// one transform, orchestrated.  Ctx supplies the thread (tid, rank), the
+// synchronisation (sync_warp, sync_cta, sync_cluster) and the HBM accesses
+// (ldg2, ldg4, stg2, stg4: streaming, the data is touched once).
+// ---------------------------------------------------------------------
+template <int T, int CX, bool VIRT, class Ctx>
+PR_HD void block_stage(Ctx& cx, float2* __restrict__ blk, int ln, const float* __restrict__ cst,
+                       const LeafConsts& K) {
+  float2 x[32];
+  fold_read<10, 5, 0, VIRT>(blk, 0, ln, x);
+  fold_compute<10, 5, 0, CX, VIRT>(x, cst, ln, K.nz);
+  cx.sync_warp();
+  fold_write<10, 5, 0, VIRT>(blk, 0, ln, x);
+  cx.sync_warp();
+  block_leaf<CX, VIRT>(blk, ln, K);
+  cx.sync_warp();
+  freq_read<5, 5, 0, VIRT>(blk, 0, ln, x);
+  freq_compute<5, 5, 0, CX, VIRT>(x, blk, 0, ln);
+  cx.sync_warp();
+  freq_write<5, 5, 0, VIRT>(blk, 0, ln, x);
+  if constexpr (VIRT) {
+    // chain levels of the trees of 32 .. 2^(T-5) values inside the block
+    for (int m = 5; m <= T - 5; ++m) {
+      cx.sync_warp();
+      block_chain_level<CX>(blk, m, ln);
+    }
+  }
+}
+
+// The CTA's region between the load and the store.  TOP: the tree dct_ot(N)
+// (CX 0) or dst_ot(N) (CX 1) of 2^T values; otherwise the rest of the D_n
+// chain: trees of 2^(T-1), 2^(T-2), ... values, the base case, and the chain
+// levels up to dct(N/2) / dst(N/2).
+template <int T, int CX, bool TOP, class Ctx>
+PR_HD void cta_transform(Ctx& cx, float2* __restrict__ reg, const float* __restrict__ cst, const LeafConsts& K) {
+  using A = BandA<T>;
+  constexpr int NW = 1 << (T - 10), NT = 1 << (T - 5);
+  constexpr bool VA = !TOP;
+  const int tid = cx.tid, ln = tid & 31, w = tid >> 5;
+  {
+    float2 x[32];
+    fold_read<A::M, A::S, A::RHO, VA>(reg, 0, tid, x);
+    fold_compute<A::M, A::S, A::RHO, CX, VA>(x, cst, tid, K.nz);
+    cx.sync_cta();
+    fold_write<A::M, A::S, A::RHO, VA>(reg, 0, tid, x);
+  }
+  cx.sync_cta();
+  float2* blk = reg + phys(w << 10);
+  if (TOP || w < NW - 1) block_stage<T, CX, false>(cx, blk, ln, cst, K);
+  else block_stage<T, CX, true>(cx, blk, ln, cst, K);
+  cx.sync_cta();
+  {
+    float2 v[32];
+    freq_read<10, A::S, A::RHO, VA>(reg, 0, tid, v);
+    freq_compute<10, A::S, A::RHO, CX, VA>(v, reg, 0, tid);
+    cx.sync_cta();
+    freq_write<10, A::S, A::RHO, VA>(reg, 0, tid, v);
+  }
+  if constexpr (!TOP) {
+    // chain levels of the trees of 2^(T-4) .. 2^(T-1) values
+    for (int m = T - 4; m <= T - 1; ++m) {
+      cx.sync_cta();
+      chain_level<CX>(reg, (1 << T) - (2 << m), m, tid, NT);
+    }
+  }
+}
+
+// region position (in its CTA) of DCT/DST sample n of an even, 0 < n < N/2:
+// the rest CTA's trees hold n = 2^t (2i + 1) at Q - 2Q/2^t + i (Sect. 6.9).
+template <int LN>
+PR_HD int rest_pos(int n) {
+  constexpr int Q = 1 << (LN - 2);
+#if defined(__CUDA_ARCH__)
+  const int t = __ffs(n) - 1;
+#else
+  const int t = __builtin_ctz((unsigned)n);
+#endif
+  return Q - ((2 * Q) >> t) + (n >> (t + 1));
+}
+
+// Load: D_c and D_r of samples [r N/8, (r+1) N/8) and their mirrors.  The
+// pair value of sample n is (a(n) + a(N-n), b(n) + b(N-n)) for the DCT
+// regions and the differences for the DST regions (Eq. qft_22-23); dc(0) =
+// x(0), dc(N/2) = x(N/2).  INV: the input is conjugated (conj F conj).
+template <int LN, bool INV, class Ctx>
+PR_HD void load_stage(Ctx& cx, const float2* __restrict__ xin, float2* const* dst, int r) {
+  constexpr int N = 1 << LN, Q = N / 4, NT = 1 << (LN - 7), NI = (N / 16) / NT;
+  const int tid = cx.tid;
+  float4 a[NI];
+  float2 m0[NI], m1[NI];
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    const int n = r * (N / 8) + 2 * (tid + i * NT);
+    a[i] = cx.ldg4(xin + n);
+    m0[i] = n > 0 ? cx.ldg2(xin + (N - n)) : make_float2(0.f, 0.f);
+    m1[i] = cx.ldg2(xin + (N - n - 1));
+  }
+  const float cj = INV ? -1.f : 1.f;
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    const int n = r * (N / 8) + 2 * (tid + i * NT);
+    const float2 xn = make_float2(a[i].x, a[i].y * cj), xo = make_float2(a[i].z, a[i].w * cj);
+    const float2 y0 = make_float2(m0[i].x, m0[i].y * cj), y1 = make_float2(m1[i].x, m1[i].y * cj);
+    // odd sample n+1: tree 0, position n/2
+    dst[0][phys(n >> 1)] = add2(xo, y1);
+    dst[2][phys(n >> 1)] = sub2(xo, y1);
+    if (n == 0) {
+      dst[1][phys(Q - 1)] = xn;  // dc(0) = x(0), the first sample of dct(2)
+    } else {
+      const int q = rest_pos<LN>(n);
+      dst[1][phys(q)] = add2(xn, y0);
+      dst[3][phys(q)] = sub2(xn, y0);
+    }
+  }
+  if (r == 3 && tid == 0) {
+    const float2 h = cx.ldg2(xin + N / 2);
+    dst[1][phys(Q)] = make_float2(h.x, h.y * cj);  // dc(N/2) = x(N/2)
+  }
+}
+
+// Store: the last chain level (M = N) from the four CTAs, D_r^F (R = DCT - i
+// DST, Eq. qft_24-25) and D_c^F (Eq. qft_17-21):
+//   X(k) = (C1 + S2, C2 - S1),  X(N-k) = (C1 - S2, C2 + S1)  at k and N/2 - k,
+// harmonics k in [r Q/4, (r+1) Q/4) in pairs, and X(N/4), X(3N/4) (rank 0).
+// INV: the output is conjugated.
+template <int LN, bool INV, class Ctx>
+PR_HD void store_stage(Ctx& cx, float2* __restrict__ xo, const float2* const* src, int r) {
+  constexpr int N = 1 << LN, Q = N / 4, NT = 1 << (LN - 7), NI = (Q / 8) / NT;
+  const int tid = cx.tid;
+  const float cj = INV ? -1.f : 1.f;
+  const float2* OC = src[0];
+  const float2* EC = src[1];
+  const float2* OS = src[2];
+  const float2* ES = src[3];
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    const int k = r * (Q / 4) + 2 * (tid + i * NT);
+    const float4 oc = *reinterpret_cast<const float4*>(OC + phys(k));
+    const float4 ec = *reinterpret_cast<const float4*>(EC + phys(k));
+    const float2 os1 = OS[phys(k)], es1 = ES[phys(k)];
+    const float2 os0 = k > 0 ? OS[phys(k - 1)] : make_float2(0.f, 0.f);
+    const float2 es0 = k > 0 ? ES[phys(k - 1)] : make_float2(0.f, 0.f);
+    float2 X0[2], XM[2], XH[2], XN[2];  // X(k+j), X(N-k-j), X(N/2-k-j), X(N/2+k+j)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const float2 o = j == 0 ? make_float2(oc.x, oc.y) : make_float2(oc.z, oc.w);
+      const float2 e = j == 0 ? make_float2(ec.x, ec.y) : make_float2(ec.z, ec.w);
+      const float2 so = j == 0 ? os0 : os1, se = j == 0 ? es0 : es1;
+      const float2 ck = add2(e, o), cm = sub2(e, o);
+      if (j == 0 && k == 0) {
+        X0[0] = make_float2(ck.x, ck.y * cj);  // X(0) = C(0)
+        XN[0] = make_float2(cm.x, cm.y * cj);  // X(N/2) = C(N/2)
+        continue;
+      }
+      const float2 sk = add2(so, se), sm = sub2(so, se);
+      X0[j] = make_float2(ck.x + sk.y, (ck.y - sk.x) * cj);
+      XM[j] = make_float2(ck.x - sk.y, (ck.y + sk.x) * cj);
+      XH[j] = make_float2(cm.x + sm.y, (cm.y - sm.x) * cj);
+      XN[j] = make_float2(cm.x - sm.y, (cm.y + sm.x) * cj);
+    }
+    cx.stg4(xo + k, make_float4(X0[0].x, X0[0].y, X0[1].x, X0[1].y));
+    cx.stg4(xo + (N / 2 + k), make_float4(XN[0].x, XN[0].y, XN[1].x, XN[1].y));
+    if (k > 0) {
+      cx.stg2(xo + (N - k), XM[0]);
+      cx.stg2(xo + (N / 2 - k), XH[0]);
+    }
+    cx.stg2(xo + (N - k - 1), XM[1]);
+    cx.stg2(xo + (N / 2 - k - 1), XH[1]);
+  }
+  if (r == 0 && tid == 0) {
+    const float2 cq = EC[phys(Q)], sq = OS[phys(Q - 1)];  // C(N/4) = E(N/4), S(N/4) = O(N/4)
+    cx.stg2(xo + Q, make_float2(cq.x + sq.y, (cq.y - sq.x) * cj));
+    cx.stg2(xo + 3 * Q, make_float2(cq.x - sq.y, (cq.y + sq.x) * cj));
+  }
+}
+
+// Shared memory of one CTA: the region (phys(2^T) + 1 float2, rounded up to
+// an even count) and the constants of node sizes 64 .. 2^T (tree 0) or
+// 64 .. 2^(T-1) (rest) as floats.
+template <int T>
+PR_HD constexpr int region_f2() {
+  return ((phys(1 << T) + 1) + 1) & ~1;
+}
+template <int T>
+PR_HD constexpr int smem_bytes() {
+  return region_f2<T>() * 8 + ((1 << T) - 32) * 4;
+}
+
+// The cluster's work: transforms cid, cid + ncl, ... of the batch.
+// reg: this CTA's region; rg4[q]: CTA q's region (distributed shared memory).
+template <int LN, bool INV, class Ctx>
+PR_HD void paired_body(Ctx& cx, const float2* __restrict__ in, float2* __restrict__ out, long long batch,
+                       long long cid, long long ncl, float2* __restrict__ reg, float* __restrict__ cst,
+                       const float* __restrict__ ctab, const LeafConsts& K, float2* const* rg4) {
+  constexpr int T = LN - 2, NT = 1 << (T - 5);
+  constexpr long long N = 1LL << LN;
+  const int r = cx.rank, tid = cx.tid;
+  const int ncst = (r & 1) == 0 ? (1 << T) - 32 : (1 << (T - 1)) - 32;
+  for (int i = tid; i < ncst; i += NT) cst[i] = ctab[30 + i];
+  for (long long t = cid; t < batch; t += ncl) {
+    cx.sync_cluster();  // the previous store has read every region
+    load_stage<LN, INV>(cx, in + t * N, rg4, r);
+    cx.sync_cluster();
+    switch (r) {
+      case 0: cta_transform<T, 0, true>(cx, reg, cst, K); break;
+      case 1: cta_transform<T, 0, false>(cx, reg, cst, K); break;
+      case 2: cta_transform<T, 1, true>(cx, reg, cst, K); break;
+      default: cta_transform<T, 1, false>(cx, reg, cst, K); break;
+    }
+    cx.sync_cluster();
+    store_stage<LN, INV>(cx, out + t * N, rg4, r);
+  }
+  cx.sync_cluster();  // keep the regions alive for the other CTAs' reads
+}
+
+}  // namespace pr
+}  // namespace amqft

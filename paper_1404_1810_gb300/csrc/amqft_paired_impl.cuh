@@ -1,0 +1,90 @@
+// Device side of the paired-region kernel (amqft_paired.cuh): the kernel,
+// its synchronisation and HBM accesses, and the persistent cluster launch.
+// Instantiated per transform length in amqft_paired_l{14,15,16}.cu.
+#pragma once
+#include "amqft_internal.h"
+#include "amqft_device.cuh"
+#include "amqft_paired.cuh"
+
+namespace amqft {
+namespace pr {
+
+struct DevCtx {
+  int tid, rank;
+  __device__ __forceinline__ void sync_warp() { __syncwarp(); }
+  __device__ __forceinline__ void sync_cta() { __syncthreads(); }
+  __device__ __forceinline__ void sync_cluster() { cg::this_cluster().sync(); }
+  __device__ __forceinline__ float4 ldg4(const float2* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
+  __device__ __forceinline__ float2 ldg2(const float2* p) { return __ldcs(p); }
+  __device__ __forceinline__ void stg4(float2* p, float4 v) { __stcs(reinterpret_cast<float4*>(p), v); }
+  __device__ __forceinline__ void stg2(float2* p, float2 v) { __stcs(p, v); }
+};
+
+// threads per CTA and CTAs per SM of the kernel for 2^LN
+__host__ __device__ constexpr int paired_tpb(int LN) { return 1 << (LN - 7); }
+__host__ __device__ constexpr int paired_ctas(int LN) { return LN >= 16 ? 1 : (LN == 15 ? 2 : 4); }
+
+template <int LN, bool INV>
+__global__ void __launch_bounds__(paired_tpb(LN), paired_ctas(LN))
+    paired_kernel(const float2* __restrict__ in, float2* __restrict__ out, long long batch,
+                  const float* __restrict__ ctab, const __grid_constant__ LeafConsts K) {
+  constexpr int T = LN - 2;
+  extern __shared__ __align__(16) float2 psm[];
+  cg::cluster_group cl = cg::this_cluster();
+  DevCtx cx{(int)threadIdx.x, (int)cl.block_rank()};
+  float2* rg4[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) rg4[q] = cl.map_shared_rank(psm, q);
+  float* cst = reinterpret_cast<float*>(psm + region_f2<T>());
+  paired_body<LN, INV>(cx, in, out, batch, (long long)(blockIdx.x >> 2), (long long)(gridDim.x >> 2), psm, cst,
+                       ctab, K, rg4);
+}
+
+template <int LN, bool INV>
+static cudaError_t launch(const float2* in, float2* out, long long batch, const float* ctab, const LeafConsts& K,
+                          cudaStream_t st) {
+  constexpr int T = LN - 2, SMEM = smem_bytes<T>();
+  auto kern = paired_kernel<LN, INV>;
+  // the number of clusters that fit on the device at once, queried once
+  static int max_clusters[2] = {0, 0};  // per INV; a race only recomputes the same value
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 4;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.blockDim = dim3(paired_tpb(LN), 1, 1);
+  cfg.dynamicSmemBytes = (size_t)SMEM;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (max_clusters[INV] == 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    if (e != cudaSuccess) return e;
+    int n = 0;
+    cfg.gridDim = dim3(4, 1, 1);
+    e = cudaOccupancyMaxActiveClusters(&n, kern, &cfg);
+    if (e != cudaSuccess) return e;
+    if (n < 1) return cudaErrorInvalidConfiguration;
+    max_clusters[INV] = n;
+  }
+  const long long ncl = batch < max_clusters[INV] ? batch : max_clusters[INV];
+  cfg.gridDim = dim3((unsigned)(4 * ncl), 1, 1);
+  return cudaLaunchKernelEx(&cfg, kern, in, out, batch, ctab, K);
+}
+
+
+template <int LN>
+cudaError_t launch_len(const void* in, void* out, long long batch, int inverse, const float* ctab,
+                       const SmallConsts& K, cudaStream_t st) {
+  LeafConsts L;
+  for (int i = 0; i < 30; ++i) L.c[i] = K.c[i];
+  L.cos_pi4 = K.cos_pi4;
+  L.nz = -0.0f;
+  const float2* x = static_cast<const float2*>(in);
+  float2* y = static_cast<float2*>(out);
+  return inverse ? launch<LN, true>(x, y, batch, ctab, L, st) : launch<LN, false>(x, y, batch, ctab, L, st);
+}
+
+}  // namespace pr
+}  // namespace amqft

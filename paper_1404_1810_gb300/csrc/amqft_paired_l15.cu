@@ -1,0 +1,9 @@
+// Paired-region kernels for N = 2^15 (own translation unit: parallel build).
+#include "amqft_paired_impl.cuh"
+
+namespace amqft {
+cudaError_t paired_launch_15(const void* in, void* out, long long batch, int inverse, const float* ctab,
+                               const SmallConsts& K, cudaStream_t st) {
+  return pr::launch_len<15>(in, out, batch, inverse, ctab, K, st);
+}
+}  // namespace amqft

@@ -544,6 +544,168 @@ PR_HD void chain_level(float2* __restrict__ sm, int P, int m, int k0, int step) 
 }
 
 // ---------------------------------------------------------------------
+// chain fold: the four chain levels m0 .. m0+3 (m0 = T-4) of a rest CTA in
+// registers.  Level m's item k (H = 2^m) reads E(k), E(H-k) (the level below)
+// and the tree values O(k), O(H-k), and gives S at k, 2H-k, H-k, H+k; its
+// S(k), S(2H-k) are E of the next level's item k, its S(H-k), S(H+k) those of
+// item H-k.  So the items of the four levels split into orbits, one per item
+// k0 of level m0, and an orbit is closed: thread k0 reads its 32 inputs,
+// the CTA synchronises, and it writes its 32 outputs of level m0+3.  The two
+// orbits with fixed points (k0 = 0 and k0 = H0/2, where items coincide or
+// sit at H/2) are run by thread 0 item by item, in place.
+// Positions: level m's tree at [P, P+H), P = 2^T - 2H; harmonic k of a DST
+// spectrum sits one position lower (DCT d = 0, DST d = 1).
+// ---------------------------------------------------------------------
+// one item, in place (any k, including the fixed points)
+template <int CX>
+PR_HD void chain_item(float2* __restrict__ sm, int P, int H, int k) {
+  constexpr int d = CX;
+  if (CX == 0 && k == 0) {
+    const float2 o = sm[phys(P)], e = sm[phys(P + H)], eH = sm[phys(P + 2 * H)];
+    sm[phys(P)] = add2(e, o);
+    sm[phys(P + 2 * H)] = sub2(e, o);
+    sm[phys(P + H)] = eH;
+    return;
+  }
+  if (k == 0) return;  // DST: S(H) = O(H) stays where it is
+  if (2 * k == H) {
+    const float2 o = sm[phys(P + k - d)], e = sm[phys(P + H + k - d)];
+    sm[phys(P + k - d)] = CX == 0 ? add2(e, o) : add2(o, e);
+    sm[phys(P + 2 * H - k - d)] = CX == 0 ? sub2(e, o) : sub2(o, e);
+    return;
+  }
+  const float2 o1 = sm[phys(P + k - d)], e1 = sm[phys(P + H + k - d)];
+  const float2 o2 = sm[phys(P + H - k - d)], e2 = sm[phys(P + 2 * H - k - d)];
+  sm[phys(P + k - d)] = CX == 0 ? add2(e1, o1) : add2(o1, e1);
+  sm[phys(P + 2 * H - k - d)] = CX == 0 ? sub2(e1, o1) : sub2(o1, e1);
+  sm[phys(P + H - k - d)] = CX == 0 ? add2(e2, o2) : add2(o2, e2);
+  sm[phys(P + H + k - d)] = CX == 0 ? sub2(e2, o2) : sub2(o2, e2);
+}
+
+// generic orbit: item (j, q) of level m0 + j is k = sg k0 + c; its inputs
+// O(k), O(H-k) sit in o[2^j - 1 + q][0..1]
+template <int T>
+struct ChainFold {
+  static constexpr int M0 = T - 4, H0 = 1 << M0;
+  PR_HD static constexpr int P(int j) { return (1 << T) - (2 * H0 << j); }
+  PR_HD static constexpr int H(int j) { return H0 << j; }
+};
+
+template <int T, int CX, int j, int q, int sg, int c>
+PR_HD void chain_fold_read(const float2* __restrict__ sm, int k0, float2 (&o)[15][2]) {
+  using F = ChainFold<T>;
+  constexpr int P = F::P(j), H = F::H(j), d = CX;
+  o[(1 << j) - 1 + q][0] = sm[phys(P + c - d + sg * k0)];
+  o[(1 << j) - 1 + q][1] = sm[phys(P + H - c - d - sg * k0)];
+  if constexpr (j < 3) {
+    chain_fold_read<T, CX, j + 1, 2 * q, sg, c>(sm, k0, o);
+    chain_fold_read<T, CX, j + 1, 2 * q + 1, -sg, H - c>(sm, k0, o);
+  }
+}
+
+template <int T, int CX, int j, int q, int sg, int c>
+PR_HD void chain_fold_run(float2* __restrict__ sm, int k0, const float2 (&o)[15][2], float2 ea, float2 eb) {
+  using F = ChainFold<T>;
+  constexpr int P = F::P(j), H = F::H(j), d = CX;
+  const float2 ok = o[(1 << j) - 1 + q][0], oh = o[(1 << j) - 1 + q][1];
+  const float2 s0 = CX == 0 ? add2(ea, ok) : add2(ok, ea);  // S(k)
+  const float2 s1 = CX == 0 ? sub2(ea, ok) : sub2(ok, ea);  // S(2H-k)
+  const float2 s2 = CX == 0 ? add2(eb, oh) : add2(oh, eb);  // S(H-k)
+  const float2 s3 = CX == 0 ? sub2(eb, oh) : sub2(oh, eb);  // S(H+k)
+  if constexpr (j < 3) {
+    chain_fold_run<T, CX, j + 1, 2 * q, sg, c>(sm, k0, o, s0, s1);
+    chain_fold_run<T, CX, j + 1, 2 * q + 1, -sg, H - c>(sm, k0, o, s2, s3);
+  } else {
+    sm[phys(P + c - d + sg * k0)] = s0;
+    sm[phys(P + 2 * H - c - d - sg * k0)] = s1;
+    sm[phys(P + H - c - d - sg * k0)] = s2;
+    sm[phys(P + H + c - d + sg * k0)] = s3;
+  }
+}
+
+// One chain level of a rest CTA with every item's reads issued before its
+// writes: item k = tid + i NT (i < H/(2 NT)) and, for thread 0, item H/2.
+// The items of a level are disjoint, so a level needs no barrier inside.
+template <int T, int CX, int m>
+PR_HD void chain_level_cta(float2* __restrict__ sm, int tid) {
+  constexpr int H = 1 << m, P = (1 << T) - 2 * H, NT = 1 << (T - 5), NI = H / 2 / NT, d = CX;
+  float2 o1[NI], e1[NI], o2[NI], e2[NI];
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    const int k = tid + i * NT;
+    o1[i] = sm[phys(P + k - d)];
+    e1[i] = sm[phys(P + H + k - d)];
+    o2[i] = sm[phys(P + H - k - d)];
+    e2[i] = sm[phys(P + 2 * H - k - d)];
+  }
+  float2 eH = make_float2(0.f, 0.f);
+  if (CX == 0 && tid == 0) eH = sm[phys(P + 2 * H)];
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    const int k = tid + i * NT;
+    if (k == 0) {
+      if (CX == 0) {  // S(0) = E(0) + O(0), S(2H) = E(0) - O(0), S(H) = E(H)
+        sm[phys(P)] = add2(e1[i], o1[i]);
+        sm[phys(P + 2 * H)] = sub2(e1[i], o1[i]);
+        sm[phys(P + H)] = eH;
+      }  // DST: no item 0; S(H) = O(H) stays in place
+      continue;
+    }
+    sm[phys(P + k - d)] = CX == 0 ? add2(e1[i], o1[i]) : add2(o1[i], e1[i]);
+    sm[phys(P + 2 * H - k - d)] = CX == 0 ? sub2(e1[i], o1[i]) : sub2(o1[i], e1[i]);
+    sm[phys(P + H - k - d)] = CX == 0 ? add2(e2[i], o2[i]) : add2(o2[i], e2[i]);
+    sm[phys(P + H + k - d)] = CX == 0 ? sub2(e2[i], o2[i]) : sub2(o2[i], e2[i]);
+  }
+  if (tid == 0) chain_item<CX>(sm, P, H, H / 2);
+}
+
+// Ctx for the synchronisation; all NT = H0/2 threads of the CTA take part
+template <int T, int CX, class Ctx>
+PR_HD void chain_fold(Ctx& cx, float2* __restrict__ sm) {
+  using F = ChainFold<T>;
+  constexpr int H0 = F::H0, d = CX;
+  const int k0 = cx.tid;
+  float2 o[15][2], ea = make_float2(0.f, 0.f), eb = make_float2(0.f, 0.f);
+  if (k0 > 0) {
+    ea = sm[phys(F::P(0) + H0 + k0 - d)];
+    eb = sm[phys(F::P(0) + 2 * H0 - k0 - d)];
+    chain_fold_read<T, CX, 0, 0, 1, 0>(sm, k0, o);
+  }
+  cx.sync_cta();
+  // recompute the write positions after the barrier instead of keeping the
+  // 32 read positions alive across it
+  int k0w = k0;
+#if defined(__CUDA_ARCH__)
+  asm volatile("mov.b32 %0, %1;" : "=r"(k0w) : "r"(k0));
+#endif
+  if (k0 > 0) {
+    chain_fold_run<T, CX, 0, 0, 1, 0>(sm, k0w, o, ea, eb);
+  } else {
+    // the orbits of items 0 and H0/2, level by level
+    constexpr int h = H0 / 2;
+    chain_item<CX>(sm, F::P(0), F::H(0), 0);
+    chain_item<CX>(sm, F::P(0), F::H(0), h);
+    chain_item<CX>(sm, F::P(1), F::H(1), 0);
+    chain_item<CX>(sm, F::P(1), F::H(1), H0);
+    chain_item<CX>(sm, F::P(1), F::H(1), h);
+    chain_item<CX>(sm, F::P(2), F::H(2), 0);
+    chain_item<CX>(sm, F::P(2), F::H(2), 2 * H0);
+    chain_item<CX>(sm, F::P(2), F::H(2), H0);
+    chain_item<CX>(sm, F::P(2), F::H(2), h);
+    chain_item<CX>(sm, F::P(2), F::H(2), 3 * h);
+    chain_item<CX>(sm, F::P(3), F::H(3), 0);
+    chain_item<CX>(sm, F::P(3), F::H(3), 4 * H0);
+    chain_item<CX>(sm, F::P(3), F::H(3), 2 * H0);
+    chain_item<CX>(sm, F::P(3), F::H(3), H0);
+    chain_item<CX>(sm, F::P(3), F::H(3), 3 * H0);
+    chain_item<CX>(sm, F::P(3), F::H(3), h);
+    chain_item<CX>(sm, F::P(3), F::H(3), 7 * h);
+    chain_item<CX>(sm, F::P(3), F::H(3), 3 * h);
+    chain_item<CX>(sm, F::P(3), F::H(3), 5 * h);
+  }
+}
+
+// ---------------------------------------------------------------------
 // stage entry points (thread index explicit; the caller synchronises
 // between the phases marked "sync")
 // ---------------------------------------------------------------------
@@ -612,7 +774,7 @@ PR_HD void block_stage(Ctx& cx, float2* __restrict__ blk, int ln, const float* _
 template <int T, int CX, bool TOP, class Ctx>
 PR_HD void cta_transform(Ctx& cx, float2* __restrict__ reg, const float* __restrict__ cst, const LeafConsts& K) {
   using A = BandA<T>;
-  constexpr int NW = 1 << (T - 10), NT = 1 << (T - 5);
+  constexpr int NW = 1 << (T - 10);
   constexpr bool VA = !TOP;
   const int tid = cx.tid, ln = tid & 31, w = tid >> 5;
   {
@@ -636,10 +798,14 @@ PR_HD void cta_transform(Ctx& cx, float2* __restrict__ reg, const float* __restr
   }
   if constexpr (!TOP) {
     // chain levels of the trees of 2^(T-4) .. 2^(T-1) values
-    for (int m = T - 4; m <= T - 1; ++m) {
-      cx.sync_cta();
-      chain_level<CX>(reg, (1 << T) - (2 << m), m, tid, NT);
-    }
+    cx.sync_cta();
+    chain_level_cta<T, CX, T - 4>(reg, tid);
+    cx.sync_cta();
+    chain_level_cta<T, CX, T - 3>(reg, tid);
+    cx.sync_cta();
+    chain_level_cta<T, CX, T - 2>(reg, tid);
+    cx.sync_cta();
+    chain_level_cta<T, CX, T - 1>(reg, tid);
   }
 }
 
@@ -660,25 +826,38 @@ PR_HD int rest_pos(int n) {
 // pair value of sample n is (a(n) + a(N-n), b(n) + b(N-n)) for the DCT
 // regions and the differences for the DST regions (Eq. qft_22-23); dc(0) =
 // x(0), dc(N/2) = x(N/2).  INV: the input is conjugated (conj F conj).
-template <int LN, bool INV, class Ctx>
-PR_HD void load_stage(Ctx& cx, const float2* __restrict__ xin, float2* const* dst, int r) {
-  constexpr int N = 1 << LN, Q = N / 4, NT = 1 << (LN - 7), NI = (N / 16) / NT;
-  const int tid = cx.tid;
+// Two rounds of HBM reads per thread: a round's reads are issued together
+// (load_fetch) and scattered into the four regions afterwards (load_scatter),
+// so the first round of the next transform can be in flight across the
+// cluster barrier that ends the current one.
+template <int LN>
+struct LoadRound {
+  static constexpr int NT = 1 << (LN - 7), NI = (1 << (LN - 4)) / NT / 2;  // items per round
   float4 a[NI];
   float2 m0[NI], m1[NI];
+};
+
+template <int LN, class Ctx>
+PR_HD void load_fetch(Ctx& cx, const float2* __restrict__ xin, int r, int round, LoadRound<LN>& R) {
+  constexpr int N = 1 << LN, NT = LoadRound<LN>::NT, NI = LoadRound<LN>::NI;
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
-    const int n = r * (N / 8) + 2 * (tid + i * NT);
-    a[i] = cx.ldg4(xin + n);
-    m0[i] = n > 0 ? cx.ldg2(xin + (N - n)) : make_float2(0.f, 0.f);
-    m1[i] = cx.ldg2(xin + (N - n - 1));
+    const int n = r * (N / 8) + 2 * (cx.tid + (round * NI + i) * NT);
+    R.a[i] = cx.ldg4(xin + n);
+    R.m0[i] = n > 0 ? cx.ldg2(xin + (N - n)) : make_float2(0.f, 0.f);
+    R.m1[i] = cx.ldg2(xin + (N - n - 1));
   }
+}
+
+template <int LN, bool INV, class Ctx>
+PR_HD void load_scatter(Ctx& cx, float2* const* dst, int r, int round, const LoadRound<LN>& R) {
+  constexpr int N = 1 << LN, Q = N / 4, NT = LoadRound<LN>::NT, NI = LoadRound<LN>::NI;
   const float cj = INV ? -1.f : 1.f;
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
-    const int n = r * (N / 8) + 2 * (tid + i * NT);
-    const float2 xn = make_float2(a[i].x, a[i].y * cj), xo = make_float2(a[i].z, a[i].w * cj);
-    const float2 y0 = make_float2(m0[i].x, m0[i].y * cj), y1 = make_float2(m1[i].x, m1[i].y * cj);
+    const int n = r * (N / 8) + 2 * (cx.tid + (round * NI + i) * NT);
+    const float2 xn = make_float2(R.a[i].x, R.a[i].y * cj), xo = make_float2(R.a[i].z, R.a[i].w * cj);
+    const float2 y0 = make_float2(R.m0[i].x, R.m0[i].y * cj), y1 = make_float2(R.m1[i].x, R.m1[i].y * cj);
     // odd sample n+1: tree 0, position n/2
     dst[0][phys(n >> 1)] = add2(xo, y1);
     dst[2][phys(n >> 1)] = sub2(xo, y1);
@@ -690,16 +869,26 @@ PR_HD void load_stage(Ctx& cx, const float2* __restrict__ xin, float2* const* ds
       dst[3][phys(q)] = sub2(xn, y0);
     }
   }
-  if (r == 3 && tid == 0) {
+}
+
+// dc(N/2) = x(N/2), the second sample of dct(2) (rank 3, thread 0)
+template <int LN, bool INV, class Ctx>
+PR_HD void load_middle(Ctx& cx, const float2* __restrict__ xin, float2* const* dst, int r) {
+  constexpr int N = 1 << LN, Q = N / 4;
+  if (r == 3 && cx.tid == 0) {
     const float2 h = cx.ldg2(xin + N / 2);
-    dst[1][phys(Q)] = make_float2(h.x, h.y * cj);  // dc(N/2) = x(N/2)
+    dst[1][phys(Q)] = make_float2(h.x, INV ? -h.y : h.y);
   }
 }
 
 // Store: the last chain level (M = N) from the four CTAs, D_r^F (R = DCT - i
 // DST, Eq. qft_24-25) and D_c^F (Eq. qft_17-21):
 //   X(k) = (C1 + S2, C2 - S1),  X(N-k) = (C1 - S2, C2 + S1)  at k and N/2 - k,
-// harmonics k in [r Q/4, (r+1) Q/4) in pairs, and X(N/4), X(3N/4) (rank 0).
+// harmonics k in [r Q/4, (r+1) Q/4), a pair (k, k+1) per thread and step,
+// and X(N/4), X(3N/4) (rank 0).  Every read is one 16-byte run of
+// distributed shared memory, consecutive lanes reading consecutive runs: the
+// DST spectra hold harmonic k at position k - 1, so a thread reads positions
+// k, k+1 (harmonics k+1, k+2) and takes harmonic k from the previous lane.
 // INV: the output is conjugated.
 template <int LN, bool INV, class Ctx>
 PR_HD void store_stage(Ctx& cx, float2* __restrict__ xo, const float2* const* src, int r) {
@@ -710,31 +899,43 @@ PR_HD void store_stage(Ctx& cx, float2* __restrict__ xo, const float2* const* sr
   const float2* EC = src[1];
   const float2* OS = src[2];
   const float2* ES = src[3];
+  float2 oc[NI][2], ec[NI][2], os[NI][3], es[NI][3];
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
     const int k = r * (Q / 4) + 2 * (tid + i * NT);
-    const float4 oc = *reinterpret_cast<const float4*>(OC + phys(k));
-    const float4 ec = *reinterpret_cast<const float4*>(EC + phys(k));
-    const float2 os1 = OS[phys(k)], es1 = ES[phys(k)];
-    const float2 os0 = k > 0 ? OS[phys(k - 1)] : make_float2(0.f, 0.f);
-    const float2 es0 = k > 0 ? ES[phys(k - 1)] : make_float2(0.f, 0.f);
+    ld_run<2>(OC, k, oc[i]);
+    ld_run<2>(EC, k, ec[i]);
+    ld_run<2>(OS, k, &os[i][1]);  // harmonics k+1, k+2
+    ld_run<2>(ES, k, &es[i][1]);
+  }
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    const int k = r * (Q / 4) + 2 * (tid + i * NT);
+    float2 po = cx.shfl_up(os[i][2], 1), pe = cx.shfl_up(es[i][2], 1);
+    if ((tid & 31) == 0) {  // harmonic k (position k - 1) of lane 0
+      po = k > 0 ? OS[phys(k - 1)] : make_float2(0.f, 0.f);
+      pe = k > 0 ? ES[phys(k - 1)] : make_float2(0.f, 0.f);
+    }
+    os[i][0] = po;
+    es[i][0] = pe;
+  }
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    const int k = r * (Q / 4) + 2 * (tid + i * NT);
     float2 X0[2], XM[2], XH[2], XN[2];  // X(k+j), X(N-k-j), X(N/2-k-j), X(N/2+k+j)
 #pragma unroll
     for (int j = 0; j < 2; ++j) {
-      const float2 o = j == 0 ? make_float2(oc.x, oc.y) : make_float2(oc.z, oc.w);
-      const float2 e = j == 0 ? make_float2(ec.x, ec.y) : make_float2(ec.z, ec.w);
-      const float2 so = j == 0 ? os0 : os1, se = j == 0 ? es0 : es1;
-      const float2 ck = add2(e, o), cm = sub2(e, o);
-      if (j == 0 && k == 0) {
-        X0[0] = make_float2(ck.x, ck.y * cj);  // X(0) = C(0)
-        XN[0] = make_float2(cm.x, cm.y * cj);  // X(N/2) = C(N/2)
-        continue;
-      }
-      const float2 sk = add2(so, se), sm = sub2(so, se);
+      const float2 ck = add2(ec[i][j], oc[i][j]), cm = sub2(ec[i][j], oc[i][j]);
+      const float2 sk = add2(os[i][j], es[i][j]), sm = sub2(os[i][j], es[i][j]);
       X0[j] = make_float2(ck.x + sk.y, (ck.y - sk.x) * cj);
       XM[j] = make_float2(ck.x - sk.y, (ck.y + sk.x) * cj);
       XH[j] = make_float2(cm.x + sm.y, (cm.y - sm.x) * cj);
       XN[j] = make_float2(cm.x - sm.y, (cm.y + sm.x) * cj);
+    }
+    if (k == 0) {  // X(0) = C(0), X(N/2) = C(N/2): the DST has no harmonic 0
+      const float2 ck = add2(ec[i][0], oc[i][0]), cm = sub2(ec[i][0], oc[i][0]);
+      X0[0] = make_float2(ck.x, ck.y * cj);
+      XN[0] = make_float2(cm.x, cm.y * cj);
     }
     cx.stg4(xo + k, make_float4(X0[0].x, X0[0].y, X0[1].x, X0[1].y));
     cx.stg4(xo + (N / 2 + k), make_float4(XN[0].x, XN[0].y, XN[1].x, XN[1].y));
@@ -768,16 +969,22 @@ PR_HD constexpr int smem_bytes() {
 // reg: this CTA's region; rg4[q]: CTA q's region (distributed shared memory).
 template <int LN, bool INV, class Ctx>
 PR_HD void paired_body(Ctx& cx, const float2* __restrict__ in, float2* __restrict__ out, long long batch,
-                       long long cid, long long ncl, float2* __restrict__ reg, float* __restrict__ cst,
+                       long long cid, long long ncl, float2* reg, float* __restrict__ cst,
                        const float* __restrict__ ctab, const LeafConsts& K, float2* const* rg4) {
   constexpr int T = LN - 2, NT = 1 << (T - 5);
   constexpr long long N = 1LL << LN;
   const int r = cx.rank, tid = cx.tid;
   const int ncst = (r & 1) == 0 ? (1 << T) - 32 : (1 << (T - 1)) - 32;
   for (int i = tid; i < ncst; i += NT) cst[i] = ctab[30 + i];
+  LoadRound<LN> R;
+  if (cid < batch) load_fetch<LN>(cx, in + cid * N, r, 0, R);
   for (long long t = cid; t < batch; t += ncl) {
+    const float2* xin = in + t * N;
     cx.sync_cluster();  // the previous store has read every region
-    load_stage<LN, INV>(cx, in + t * N, rg4, r);
+    load_scatter<LN, INV>(cx, rg4, r, 0, R);
+    load_fetch<LN>(cx, xin, r, 1, R);
+    load_middle<LN, INV>(cx, xin, rg4, r);
+    load_scatter<LN, INV>(cx, rg4, r, 1, R);
     cx.sync_cluster();
     switch (r) {
       case 0: cta_transform<T, 0, true>(cx, reg, cst, K); break;
@@ -787,6 +994,8 @@ PR_HD void paired_body(Ctx& cx, const float2* __restrict__ in, float2* __restric
     }
     cx.sync_cluster();
     store_stage<LN, INV>(cx, out + t * N, rg4, r);
+    // the next transform's first reads fly across the barrier at the loop top
+    if (t + ncl < batch) load_fetch<LN>(cx, in + (t + ncl) * N, r, 0, R);
   }
   cx.sync_cluster();  // keep the regions alive for the other CTAs' reads
 }

@@ -18,6 +18,9 @@ struct DevCtx {
   __device__ __forceinline__ float2 ldg2(const float2* p) { return __ldcs(p); }
   __device__ __forceinline__ void stg4(float2* p, float4 v) { __stcs(reinterpret_cast<float4*>(p), v); }
   __device__ __forceinline__ void stg2(float2* p, float2 v) { __stcs(p, v); }
+  __device__ __forceinline__ float2 shfl_up(float2 v, int d) {
+    return make_float2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+  }
 };
 
 // threads per CTA and CTAs per SM of the kernel for 2^LN
@@ -34,7 +37,9 @@ __global__ void __launch_bounds__(paired_tpb(LN), paired_ctas(LN))
   DevCtx cx{(int)threadIdx.x, (int)cl.block_rank()};
   float2* rg4[4];
 #pragma unroll
-  for (int q = 0; q < 4; ++q) rg4[q] = cl.map_shared_rank(psm, q);
+  // the CTA's own region through the local shared-memory window, the other
+  // three through distributed shared memory
+  for (int q = 0; q < 4; ++q) rg4[q] = q == (int)cl.block_rank() ? psm : cl.map_shared_rank(psm, q);
   float* cst = reinterpret_cast<float*>(psm + region_f2<T>());
   paired_body<LN, INV>(cx, in, out, batch, (long long)(blockIdx.x >> 2), (long long)(gridDim.x >> 2), psm, cst,
                        ctab, K, rg4);

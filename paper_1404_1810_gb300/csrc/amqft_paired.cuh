@@ -544,19 +544,13 @@ PR_HD void chain_level(float2* __restrict__ sm, int P, int m, int k0, int step) 
 }
 
 // ---------------------------------------------------------------------
-// chain fold: the four chain levels m0 .. m0+3 (m0 = T-4) of a rest CTA in
-// registers.  Level m's item k (H = 2^m) reads E(k), E(H-k) (the level below)
-// and the tree values O(k), O(H-k), and gives S at k, 2H-k, H-k, H+k; its
-// S(k), S(2H-k) are E of the next level's item k, its S(H-k), S(H+k) those of
-// item H-k.  So the items of the four levels split into orbits, one per item
-// k0 of level m0, and an orbit is closed: thread k0 reads its 32 inputs,
-// the CTA synchronises, and it writes its 32 outputs of level m0+3.  The two
-// orbits with fixed points (k0 = 0 and k0 = H0/2, where items coincide or
-// sit at H/2) are run by thread 0 item by item, in place.
-// Positions: level m's tree at [P, P+H), P = 2^T - 2H; harmonic k of a DST
-// spectrum sits one position lower (DCT d = 0, DST d = 1).
+// chain levels of a rest CTA.  Level m's item k (H = 2^m) reads E(k), E(H-k)
+// (the chain below) and the tree values O(k), O(H-k), and gives S at k,
+// 2H-k, H-k, H+k, in place.  Positions: level m's tree at [P, P+H),
+// P = 2^T - 2H; harmonic k of a DST spectrum sits one position lower
+// (DCT d = 0, DST d = 1).
 // ---------------------------------------------------------------------
-// one item, in place (any k, including the fixed points)
+// one item, in place (any k, including k = 0 and k = H/2)
 template <int CX>
 PR_HD void chain_item(float2* __restrict__ sm, int P, int H, int k) {
   constexpr int d = CX;
@@ -580,47 +574,6 @@ PR_HD void chain_item(float2* __restrict__ sm, int P, int H, int k) {
   sm[phys(P + 2 * H - k - d)] = CX == 0 ? sub2(e1, o1) : sub2(o1, e1);
   sm[phys(P + H - k - d)] = CX == 0 ? add2(e2, o2) : add2(o2, e2);
   sm[phys(P + H + k - d)] = CX == 0 ? sub2(e2, o2) : sub2(o2, e2);
-}
-
-// generic orbit: item (j, q) of level m0 + j is k = sg k0 + c; its inputs
-// O(k), O(H-k) sit in o[2^j - 1 + q][0..1]
-template <int T>
-struct ChainFold {
-  static constexpr int M0 = T - 4, H0 = 1 << M0;
-  PR_HD static constexpr int P(int j) { return (1 << T) - (2 * H0 << j); }
-  PR_HD static constexpr int H(int j) { return H0 << j; }
-};
-
-template <int T, int CX, int j, int q, int sg, int c>
-PR_HD void chain_fold_read(const float2* __restrict__ sm, int k0, float2 (&o)[15][2]) {
-  using F = ChainFold<T>;
-  constexpr int P = F::P(j), H = F::H(j), d = CX;
-  o[(1 << j) - 1 + q][0] = sm[phys(P + c - d + sg * k0)];
-  o[(1 << j) - 1 + q][1] = sm[phys(P + H - c - d - sg * k0)];
-  if constexpr (j < 3) {
-    chain_fold_read<T, CX, j + 1, 2 * q, sg, c>(sm, k0, o);
-    chain_fold_read<T, CX, j + 1, 2 * q + 1, -sg, H - c>(sm, k0, o);
-  }
-}
-
-template <int T, int CX, int j, int q, int sg, int c>
-PR_HD void chain_fold_run(float2* __restrict__ sm, int k0, const float2 (&o)[15][2], float2 ea, float2 eb) {
-  using F = ChainFold<T>;
-  constexpr int P = F::P(j), H = F::H(j), d = CX;
-  const float2 ok = o[(1 << j) - 1 + q][0], oh = o[(1 << j) - 1 + q][1];
-  const float2 s0 = CX == 0 ? add2(ea, ok) : add2(ok, ea);  // S(k)
-  const float2 s1 = CX == 0 ? sub2(ea, ok) : sub2(ok, ea);  // S(2H-k)
-  const float2 s2 = CX == 0 ? add2(eb, oh) : add2(oh, eb);  // S(H-k)
-  const float2 s3 = CX == 0 ? sub2(eb, oh) : sub2(oh, eb);  // S(H+k)
-  if constexpr (j < 3) {
-    chain_fold_run<T, CX, j + 1, 2 * q, sg, c>(sm, k0, o, s0, s1);
-    chain_fold_run<T, CX, j + 1, 2 * q + 1, -sg, H - c>(sm, k0, o, s2, s3);
-  } else {
-    sm[phys(P + c - d + sg * k0)] = s0;
-    sm[phys(P + 2 * H - c - d - sg * k0)] = s1;
-    sm[phys(P + H - c - d - sg * k0)] = s2;
-    sm[phys(P + H + c - d + sg * k0)] = s3;
-  }
 }
 
 // One chain level of a rest CTA with every item's reads issued before its
@@ -657,52 +610,6 @@ PR_HD void chain_level_cta(float2* __restrict__ sm, int tid) {
     sm[phys(P + H + k - d)] = CX == 0 ? sub2(e2[i], o2[i]) : sub2(o2[i], e2[i]);
   }
   if (tid == 0) chain_item<CX>(sm, P, H, H / 2);
-}
-
-// Ctx for the synchronisation; all NT = H0/2 threads of the CTA take part
-template <int T, int CX, class Ctx>
-PR_HD void chain_fold(Ctx& cx, float2* __restrict__ sm) {
-  using F = ChainFold<T>;
-  constexpr int H0 = F::H0, d = CX;
-  const int k0 = cx.tid;
-  float2 o[15][2], ea = make_float2(0.f, 0.f), eb = make_float2(0.f, 0.f);
-  if (k0 > 0) {
-    ea = sm[phys(F::P(0) + H0 + k0 - d)];
-    eb = sm[phys(F::P(0) + 2 * H0 - k0 - d)];
-    chain_fold_read<T, CX, 0, 0, 1, 0>(sm, k0, o);
-  }
-  cx.sync_cta();
-  // recompute the write positions after the barrier instead of keeping the
-  // 32 read positions alive across it
-  int k0w = k0;
-#if defined(__CUDA_ARCH__)
-  asm volatile("mov.b32 %0, %1;" : "=r"(k0w) : "r"(k0));
-#endif
-  if (k0 > 0) {
-    chain_fold_run<T, CX, 0, 0, 1, 0>(sm, k0w, o, ea, eb);
-  } else {
-    // the orbits of items 0 and H0/2, level by level
-    constexpr int h = H0 / 2;
-    chain_item<CX>(sm, F::P(0), F::H(0), 0);
-    chain_item<CX>(sm, F::P(0), F::H(0), h);
-    chain_item<CX>(sm, F::P(1), F::H(1), 0);
-    chain_item<CX>(sm, F::P(1), F::H(1), H0);
-    chain_item<CX>(sm, F::P(1), F::H(1), h);
-    chain_item<CX>(sm, F::P(2), F::H(2), 0);
-    chain_item<CX>(sm, F::P(2), F::H(2), 2 * H0);
-    chain_item<CX>(sm, F::P(2), F::H(2), H0);
-    chain_item<CX>(sm, F::P(2), F::H(2), h);
-    chain_item<CX>(sm, F::P(2), F::H(2), 3 * h);
-    chain_item<CX>(sm, F::P(3), F::H(3), 0);
-    chain_item<CX>(sm, F::P(3), F::H(3), 4 * H0);
-    chain_item<CX>(sm, F::P(3), F::H(3), 2 * H0);
-    chain_item<CX>(sm, F::P(3), F::H(3), H0);
-    chain_item<CX>(sm, F::P(3), F::H(3), 3 * H0);
-    chain_item<CX>(sm, F::P(3), F::H(3), h);
-    chain_item<CX>(sm, F::P(3), F::H(3), 7 * h);
-    chain_item<CX>(sm, F::P(3), F::H(3), 3 * h);
-    chain_item<CX>(sm, F::P(3), F::H(3), 5 * h);
-  }
 }
 
 // ---------------------------------------------------------------------

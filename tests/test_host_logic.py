@@ -74,3 +74,24 @@ def test_expected_exponent_puts_the_maximum_in_range():
     assert expected_exponent(np.array([1j * -3.0 * 2.0 ** 20], np.complex64)) == 8
     assert expected_exponent(np.zeros(4, np.complex64)) == 0
     assert expected_exponent(np.array([np.inf, 1.0], np.complex64)) == 0
+
+
+def test_sine_scan_check_rejects_mismatches():
+    """The check used for variants 5 and 7 beyond 2^9 fails on a non-finite
+    pattern that differs from the float32 recursion and on an error far from
+    the recursion's own; it passes on the recursion itself."""
+    import numpy as np
+    import pytest
+
+    from gpu_util import sine_scan_check
+
+    rng = np.random.default_rng(3)
+    r64 = rng.standard_normal(256) + 1j * rng.standard_normal(256)
+    r32 = r64 + 1e-3 * (rng.standard_normal(256) + 1j * rng.standard_normal(256))
+    sine_scan_check(r32.copy(), r32, r64, "same")
+    bad = r32.copy()
+    bad[7] = np.nan
+    with pytest.raises(AssertionError):
+        sine_scan_check(bad, r32, r64, "nan")
+    with pytest.raises(AssertionError):
+        sine_scan_check(r64 + 10.0 * (r32 - r64), r32, r64, "x10")

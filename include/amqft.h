@@ -213,9 +213,11 @@ int amqft_ragged_skipped(amqft_plan_t plan, int64_t *skipped);
  * its own batch is ignored: create it with batch 0 so that it holds no
  * workspace.  in/out: device pointers to batch * 2^log2n interleaved complex
  * float32 values, owned by the caller, 8-byte aligned, not overlapping.
- * Makes no device or host allocation.  The first call on a device looks up
- * the scratch array's address (and so may load the library's module into the
- * context); make it before any stream capture.  The scratch is shared by
+ * Makes no device or host allocation.  Every call looks up the scratch
+ * array's address in the current context (a host-side lookup, never cached,
+ * so a reset device is safe); the first call on a device may load the
+ * library's module into the context, so make it before any stream capture.
+ * The scratch is shared by
  * every plan on the device: calls that overlap in time (different streams, or
  * host threads without ordering) race; calls on one stream are ordered.
  * Nothing in the scratch needs to start at zero.

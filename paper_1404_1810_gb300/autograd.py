@@ -7,29 +7,47 @@ convention for complex tensors).  F^H = conj o F o conj is exactly the
 library's unnormalised inverse (amqft_exec_inv), so the backward pass is one
 launch of the same fused recursion; the backward of the inverse transform is
 the forward transform.
+
+Ordering: the transforms run on the current CUDA stream.  A cached plan above
+2^16 owns a multi-pass workspace that its calls share, so forward and
+backward passes that use one plan must be ordered (one stream, or explicit
+synchronisation between streams and host threads).
 """
 from __future__ import annotations
 
 import threading
+from collections import OrderedDict
 
 from .amqft import Plan
 
 _lock = threading.Lock()
-_plans: dict = {}
+_plans: "OrderedDict[tuple, Plan]" = OrderedDict()
+
+# At most this many cached plans: a plan above 2^16 holds a workspace of up
+# to 2 GiB, so the least recently used plan is released beyond the bound.
+MAX_CACHED_PLANS = 8
 
 
 def plan_for(log2n: int, variant: int, batch: int, device_index: int) -> Plan:
     """Cached plan for (length, variant, batch, device): plans own device
-    constant tables, so repeated calls reuse them."""
+    constant tables (and, above 2^16, a workspace), so repeated calls reuse
+    them; the cache keeps the MAX_CACHED_PLANS most recently used."""
     import torch
 
     key = (int(log2n), int(variant), int(batch), int(device_index))
     with _lock:
         p = _plans.get(key)
-        if p is None:
-            with torch.cuda.device(device_index):
-                p = Plan(log2n, variant, batch)
-            _plans[key] = p
+        if p is not None:
+            _plans.move_to_end(key)
+            return p
+        with torch.cuda.device(device_index):
+            p = Plan(log2n, variant, batch)
+        _plans[key] = p
+        while len(_plans) > MAX_CACHED_PLANS:
+            old_key, old = _plans.popitem(last=False)
+            with torch.cuda.device(old_key[3]):
+                torch.cuda.synchronize()  # no kernel of the released plan is in flight
+            old.close()
         return p
 
 

@@ -23,8 +23,6 @@
 // without ordering) race on the scratch; calls on one stream are ordered.
 #include <stdint.h>
 
-#include <mutex>
-
 #include "amqft.h"
 #include "amqft_internal.h"
 #include "amqft_multipass_impl.cuh"
@@ -39,21 +37,15 @@ static_assert(AMQFT_STATIC_SCRATCH_FLOATS == 2LL * 2 * 4 * ((1LL << (AMQFT_STATI
 // loaded into each device's context), zero-filled at load and never freed.
 static __device__ __align__(256) float g_scratch[AMQFT_STATIC_SCRATCH_FLOATS];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-float* g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of g_scratch on device `dev` (the current device), looked up
-// once per device.
-cudaError_t scratch_for(int dev, float** out) {
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<float*>(p);
-  }
-  *out = g_scratch_ptr[dev];
+// Device address of g_scratch in the current context.  Looked up on every
+// call (a host-side lookup) rather than cached, so that a context destroyed
+// and recreated (cudaDeviceReset, a framework resetting the device) never
+// leaves a stale address behind.
+cudaError_t scratch_address(float** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+  if (e != cudaSuccess) return e;
+  *out = static_cast<float*>(p);
   return cudaSuccess;
 }
 
@@ -100,10 +92,8 @@ extern "C" int amqft_exec_static(amqft_plan_t plan, int64_t batch, const void* i
   if (dev != pv.device)
     return set_error(AMQFT_ERR_DEVICE, "amqft_exec_static: current device %d, plan was made on device %d", dev,
                      pv.device);
-  if (dev < 0 || dev >= kMaxDevices)
-    return set_error(AMQFT_ERR_DEVICE, "amqft_exec_static: device %d beyond the %d supported", dev, kMaxDevices);
   float* scratch = nullptr;
-  e = scratch_for(dev, &scratch);
+  e = scratch_address(&scratch);
   if (e != cudaSuccess)
     return set_error(AMQFT_ERR_CUDA, "amqft_exec_static: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
   // same region geometry as a plan's own workspace

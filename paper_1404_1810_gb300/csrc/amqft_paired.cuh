@@ -586,6 +586,10 @@ PR_HD void chain_level_cta(float2* __restrict__ sm, int tid) {
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
     const int k = tid + i * NT;
+    if (CX == 1 && k == 0) {  // the DST has no item 0 (its positions would start at P - 1)
+      o1[i] = e1[i] = o2[i] = e2[i] = make_float2(0.f, 0.f);
+      continue;
+    }
     o1[i] = sm[phys(P + k - d)];
     e1[i] = sm[phys(P + H + k - d)];
     o2[i] = sm[phys(P + H - k - d)];
@@ -733,13 +737,13 @@ PR_HD int rest_pos(int n) {
 // pair value of sample n is (a(n) + a(N-n), b(n) + b(N-n)) for the DCT
 // regions and the differences for the DST regions (Eq. qft_22-23); dc(0) =
 // x(0), dc(N/2) = x(N/2).  INV: the input is conjugated (conj F conj).
-// Two rounds of HBM reads per thread: a round's reads are issued together
+// Four rounds of HBM reads per thread: a round's reads are issued together
 // (load_fetch) and scattered into the four regions afterwards (load_scatter),
-// so the first round of the next transform can be in flight across the
-// cluster barrier that ends the current one.
+// and the first round of the next transform is in flight across the cluster
+// barrier that ends the current one.
 template <int LN>
 struct LoadRound {
-  static constexpr int NT = 1 << (LN - 7), NI = (1 << (LN - 4)) / NT / 2;  // items per round
+  static constexpr int NT = 1 << (LN - 7), NI = (1 << (LN - 4)) / NT / 4;  // items per round
   float4 a[NI];
   float2 m0[NI], m1[NI];
 };
@@ -757,7 +761,7 @@ PR_HD void load_fetch(Ctx& cx, const float2* __restrict__ xin, int r, int round,
 }
 
 template <int LN, bool INV, class Ctx>
-PR_HD void load_scatter(Ctx& cx, float2* const* dst, int r, int round, const LoadRound<LN>& R) {
+PR_HD void load_scatter(Ctx& cx, int r, int round, const LoadRound<LN>& R) {
   constexpr int N = 1 << LN, Q = N / 4, NT = LoadRound<LN>::NT, NI = LoadRound<LN>::NI;
   const float cj = INV ? -1.f : 1.f;
 #pragma unroll
@@ -766,25 +770,25 @@ PR_HD void load_scatter(Ctx& cx, float2* const* dst, int r, int round, const Loa
     const float2 xn = make_float2(R.a[i].x, R.a[i].y * cj), xo = make_float2(R.a[i].z, R.a[i].w * cj);
     const float2 y0 = make_float2(R.m0[i].x, R.m0[i].y * cj), y1 = make_float2(R.m1[i].x, R.m1[i].y * cj);
     // odd sample n+1: tree 0, position n/2
-    dst[0][phys(n >> 1)] = add2(xo, y1);
-    dst[2][phys(n >> 1)] = sub2(xo, y1);
+    cx.dst2(0, phys(n >> 1), add2(xo, y1));
+    cx.dst2(2, phys(n >> 1), sub2(xo, y1));
     if (n == 0) {
-      dst[1][phys(Q - 1)] = xn;  // dc(0) = x(0), the first sample of dct(2)
+      cx.dst2(1, phys(Q - 1), xn);  // dc(0) = x(0), the first sample of dct(2)
     } else {
       const int q = rest_pos<LN>(n);
-      dst[1][phys(q)] = add2(xn, y0);
-      dst[3][phys(q)] = sub2(xn, y0);
+      cx.dst2(1, phys(q), add2(xn, y0));
+      cx.dst2(3, phys(q), sub2(xn, y0));
     }
   }
 }
 
 // dc(N/2) = x(N/2), the second sample of dct(2) (rank 3, thread 0)
 template <int LN, bool INV, class Ctx>
-PR_HD void load_middle(Ctx& cx, const float2* __restrict__ xin, float2* const* dst, int r) {
+PR_HD void load_middle(Ctx& cx, const float2* __restrict__ xin, int r) {
   constexpr int N = 1 << LN, Q = N / 4;
   if (r == 3 && cx.tid == 0) {
     const float2 h = cx.ldg2(xin + N / 2);
-    dst[1][phys(Q)] = make_float2(h.x, INV ? -h.y : h.y);
+    cx.dst2(1, phys(Q), make_float2(h.x, INV ? -h.y : h.y));
   }
 }
 
@@ -798,30 +802,26 @@ PR_HD void load_middle(Ctx& cx, const float2* __restrict__ xin, float2* const* d
 // k, k+1 (harmonics k+1, k+2) and takes harmonic k from the previous lane.
 // INV: the output is conjugated.
 template <int LN, bool INV, class Ctx>
-PR_HD void store_stage(Ctx& cx, float2* __restrict__ xo, const float2* const* src, int r) {
+PR_HD void store_stage(Ctx& cx, float2* __restrict__ xo, int r) {
   constexpr int N = 1 << LN, Q = N / 4, NT = 1 << (LN - 7), NI = (Q / 8) / NT;
   const int tid = cx.tid;
   const float cj = INV ? -1.f : 1.f;
-  const float2* OC = src[0];
-  const float2* EC = src[1];
-  const float2* OS = src[2];
-  const float2* ES = src[3];
   float2 oc[NI][2], ec[NI][2], os[NI][3], es[NI][3];
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
     const int k = r * (Q / 4) + 2 * (tid + i * NT);
-    ld_run<2>(OC, k, oc[i]);
-    ld_run<2>(EC, k, ec[i]);
-    ld_run<2>(OS, k, &os[i][1]);  // harmonics k+1, k+2
-    ld_run<2>(ES, k, &es[i][1]);
+    cx.dld4(0, phys(k), oc[i]);
+    cx.dld4(1, phys(k), ec[i]);
+    cx.dld4(2, phys(k), &os[i][1]);  // harmonics k+1, k+2
+    cx.dld4(3, phys(k), &es[i][1]);
   }
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
     const int k = r * (Q / 4) + 2 * (tid + i * NT);
     float2 po = cx.shfl_up(os[i][2], 1), pe = cx.shfl_up(es[i][2], 1);
     if ((tid & 31) == 0) {  // harmonic k (position k - 1) of lane 0
-      po = k > 0 ? OS[phys(k - 1)] : make_float2(0.f, 0.f);
-      pe = k > 0 ? ES[phys(k - 1)] : make_float2(0.f, 0.f);
+      po = k > 0 ? cx.dld2(2, phys(k - 1)) : make_float2(0.f, 0.f);
+      pe = k > 0 ? cx.dld2(3, phys(k - 1)) : make_float2(0.f, 0.f);
     }
     os[i][0] = po;
     es[i][0] = pe;
@@ -854,7 +854,7 @@ PR_HD void store_stage(Ctx& cx, float2* __restrict__ xo, const float2* const* sr
     cx.stg2(xo + (N / 2 - k - 1), XH[1]);
   }
   if (r == 0 && tid == 0) {
-    const float2 cq = EC[phys(Q)], sq = OS[phys(Q - 1)];  // C(N/4) = E(N/4), S(N/4) = O(N/4)
+    const float2 cq = cx.dld2(1, phys(Q)), sq = cx.dld2(2, phys(Q - 1));  // C(N/4) = E(N/4), S(N/4) = O(N/4)
     cx.stg2(xo + Q, make_float2(cq.x + sq.y, (cq.y - sq.x) * cj));
     cx.stg2(xo + 3 * Q, make_float2(cq.x - sq.y, (cq.y + sq.x) * cj));
   }
@@ -873,11 +873,12 @@ PR_HD constexpr int smem_bytes() {
 }
 
 // The cluster's work: transforms cid, cid + ncl, ... of the batch.
-// reg: this CTA's region; rg4[q]: CTA q's region (distributed shared memory).
+// reg: this CTA's region; Ctx reaches CTA q's region with dst2 / dld2 / dld4
+// (float2 index into the region: distributed shared memory for the others).
 template <int LN, bool INV, class Ctx>
 PR_HD void paired_body(Ctx& cx, const float2* __restrict__ in, float2* __restrict__ out, long long batch,
                        long long cid, long long ncl, float2* reg, float* __restrict__ cst,
-                       const float* __restrict__ ctab, const LeafConsts& K, float2* const* rg4) {
+                       const float* __restrict__ ctab, const LeafConsts& K) {
   constexpr int T = LN - 2, NT = 1 << (T - 5);
   constexpr long long N = 1LL << LN;
   const int r = cx.rank, tid = cx.tid;
@@ -888,10 +889,13 @@ PR_HD void paired_body(Ctx& cx, const float2* __restrict__ in, float2* __restric
   for (long long t = cid; t < batch; t += ncl) {
     const float2* xin = in + t * N;
     cx.sync_cluster();  // the previous store has read every region
-    load_scatter<LN, INV>(cx, rg4, r, 0, R);
-    load_fetch<LN>(cx, xin, r, 1, R);
-    load_middle<LN, INV>(cx, xin, rg4, r);
-    load_scatter<LN, INV>(cx, rg4, r, 1, R);
+    load_scatter<LN, INV>(cx, r, 0, R);
+#pragma unroll
+    for (int rd = 1; rd < 4; ++rd) {
+      load_fetch<LN>(cx, xin, r, rd, R);
+      load_scatter<LN, INV>(cx, r, rd, R);
+    }
+    load_middle<LN, INV>(cx, xin, r);
     cx.sync_cluster();
     switch (r) {
       case 0: cta_transform<T, 0, true>(cx, reg, cst, K); break;
@@ -900,7 +904,7 @@ PR_HD void paired_body(Ctx& cx, const float2* __restrict__ in, float2* __restric
       default: cta_transform<T, 1, false>(cx, reg, cst, K); break;
     }
     cx.sync_cluster();
-    store_stage<LN, INV>(cx, out + t * N, rg4, r);
+    store_stage<LN, INV>(cx, out + t * N, r);
     // the next transform's first reads fly across the barrier at the loop top
     if (t + ncl < batch) load_fetch<LN>(cx, in + (t + ncl) * N, r, 0, R);
   }

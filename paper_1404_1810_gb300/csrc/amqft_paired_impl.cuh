@@ -11,6 +11,8 @@ namespace pr {
 
 struct DevCtx {
   int tid, rank;
+  unsigned lbase;     // shared-window address of this CTA's region
+  unsigned cbase[4];  // shared::cluster addresses of the four regions
   __device__ __forceinline__ void sync_warp() { __syncwarp(); }
   __device__ __forceinline__ void sync_cta() { __syncthreads(); }
   __device__ __forceinline__ void sync_cluster() { cg::this_cluster().sync(); }
@@ -20,6 +22,36 @@ struct DevCtx {
   __device__ __forceinline__ void stg2(float2* p, float2 v) { __stcs(p, v); }
   __device__ __forceinline__ float2 shfl_up(float2 v, int d) {
     return make_float2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+  }
+  // float2 index i of CTA q's region: the own region through the shared
+  // window, the others as distributed shared memory, 32-bit addresses
+  __device__ __forceinline__ void dst2(int q, int i, float2 v) {
+    if (q == rank)
+      asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(lbase + 8u * (unsigned)i), "f"(v.x), "f"(v.y) : "memory");
+    else
+      asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(cbase[q] + 8u * (unsigned)i), "f"(v.x), "f"(v.y)
+                   : "memory");
+  }
+  __device__ __forceinline__ float2 dld2(int q, int i) {
+    float2 v;
+    if (q == rank)
+      asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(lbase + 8u * (unsigned)i) : "memory");
+    else
+      asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(cbase[q] + 8u * (unsigned)i)
+                   : "memory");
+    return v;
+  }
+  // two float2 at index i (even): one 16-byte access
+  __device__ __forceinline__ void dld4(int q, int i, float2* v) {
+    float a, b, c, d;
+    if (q == rank)
+      asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(a), "=f"(b), "=f"(c), "=f"(d)
+                   : "r"(lbase + 8u * (unsigned)i) : "memory");
+    else
+      asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(a), "=f"(b), "=f"(c), "=f"(d)
+                   : "r"(cbase[q] + 8u * (unsigned)i) : "memory");
+    v[0] = make_float2(a, b);
+    v[1] = make_float2(c, d);
   }
 };
 
@@ -34,15 +66,16 @@ __global__ void __launch_bounds__(paired_tpb(LN), paired_ctas(LN))
   constexpr int T = LN - 2;
   extern __shared__ __align__(16) float2 psm[];
   cg::cluster_group cl = cg::this_cluster();
-  DevCtx cx{(int)threadIdx.x, (int)cl.block_rank()};
-  float2* rg4[4];
+  DevCtx cx;
+  cx.tid = (int)threadIdx.x;
+  cx.rank = (int)cl.block_rank();
+  cx.lbase = (unsigned)__cvta_generic_to_shared(psm);
 #pragma unroll
-  // the CTA's own region through the local shared-memory window, the other
-  // three through distributed shared memory
-  for (int q = 0; q < 4; ++q) rg4[q] = q == (int)cl.block_rank() ? psm : cl.map_shared_rank(psm, q);
+  for (int q = 0; q < 4; ++q)
+    asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(cx.cbase[q]) : "r"(cx.lbase), "r"(q));
   float* cst = reinterpret_cast<float*>(psm + region_f2<T>());
   paired_body<LN, INV>(cx, in, out, batch, (long long)(blockIdx.x >> 2), (long long)(gridDim.x >> 2), psm, cst,
-                       ctab, K, rg4);
+                       ctab, K);
 }
 
 template <int LN, bool INV>

@@ -95,3 +95,38 @@ def test_sine_scan_check_rejects_mismatches():
         sine_scan_check(bad, r32, r64, "nan")
     with pytest.raises(AssertionError):
         sine_scan_check(r64 + 10.0 * (r32 - r64), r32, r64, "x10")
+
+
+def test_autograd_plan_cache_is_bounded(monkeypatch):
+    """The autograd plan cache keeps the most recently used plans and closes
+    the least recently used one beyond its bound (fake plans, no GPU)."""
+    import contextlib
+
+    import torch
+
+    from paper_1404_1810_gb300 import autograd
+
+    closed = []
+
+    class FakePlan:
+        def __init__(self, log2n, variant, batch):
+            self.key = (log2n, variant, batch)
+
+        def close(self):
+            closed.append(self.key)
+
+    monkeypatch.setattr(autograd, "Plan", FakePlan)
+    monkeypatch.setattr(torch.cuda, "device", lambda i: contextlib.nullcontext())
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    autograd._plans.clear()
+    try:
+        first = autograd.plan_for(10, 4, 1, 0)
+        for b in range(2, 2 + autograd.MAX_CACHED_PLANS):
+            autograd.plan_for(10, 4, b, 0)
+            if b == 3:
+                assert autograd.plan_for(10, 4, 1, 0) is first   # reuse refreshes the entry
+        assert len(autograd._plans) == autograd.MAX_CACHED_PLANS
+        assert closed == [(10, 4, 2)]                             # least recently used went first
+        assert autograd.plan_for(10, 4, 1, 0) is first
+    finally:
+        autograd._plans.clear()

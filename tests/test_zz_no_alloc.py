@@ -63,6 +63,39 @@ def test_static_matches_plan_exec(lib, log2n, variant, batch):
         amqft_destroy(h)
 
 
+def test_static_allocates_nothing(lib):
+    """A batch-0 plan holds its constant table only, and calls of
+    amqft_exec_static take no device memory (free memory measured by the
+    driver before and after, once a warm-up call has loaded the module)."""
+    import torch
+
+    from paper_1404_1810_gb300 import amqft_destroy, amqft_exec_static, amqft_plan
+
+    log2n, batch = 18, 4
+    n = 1 << log2n
+    x = synth.device_normal_complex64(n, batch, "cuda", seed_offset=5)
+    out = torch.empty_like(x)
+    st = torch.cuda.current_stream().cuda_stream
+    h = amqft_plan(log2n, 4, 0)
+    try:
+        amqft_exec_static(h, batch, x.data_ptr(), out.data_ptr(), 0, st)   # warm-up: module loaded
+        torch.cuda.synchronize()
+    finally:
+        amqft_destroy(h)
+    free0 = torch.cuda.mem_get_info()[0]
+    h = amqft_plan(log2n, 4, 0)
+    try:
+        table = (n // 4 - 2) * 4
+        free1 = torch.cuda.mem_get_info()[0]
+        assert free0 - free1 <= table + (4 << 20), "a batch-0 plan holds more than its constant table"
+        for inverse in (0, 1, 0):
+            amqft_exec_static(h, batch, x.data_ptr(), out.data_ptr(), inverse, st)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free1, "amqft_exec_static took device memory"
+    finally:
+        amqft_destroy(h)
+
+
 def test_static_rejects_what_it_cannot_hold(lib):
     import torch
 

@@ -803,55 +803,59 @@ PR_HD void load_middle(Ctx& cx, const float2* __restrict__ xin, int r) {
 // INV: the output is conjugated.
 template <int LN, bool INV, class Ctx>
 PR_HD void store_stage(Ctx& cx, float2* __restrict__ xo, int r) {
-  constexpr int N = 1 << LN, Q = N / 4, NT = 1 << (LN - 7), NI = (Q / 8) / NT;
+  constexpr int N = 1 << LN, Q = N / 4, NT = 1 << (LN - 7), NALL = (Q / 8) / NT;
+  constexpr int NI = NALL < 2 ? NALL : 2;  // pairs in flight per thread (register budget)
   const int tid = cx.tid;
   const float cj = INV ? -1.f : 1.f;
-  float2 oc[NI][2], ec[NI][2], os[NI][3], es[NI][3];
+#pragma unroll 1
+  for (int g = 0; g < NALL / NI; ++g) {
+    float2 oc[NI][2], ec[NI][2], os[NI][3], es[NI][3];
 #pragma unroll
-  for (int i = 0; i < NI; ++i) {
-    const int k = r * (Q / 4) + 2 * (tid + i * NT);
-    cx.dld4(0, phys(k), oc[i]);
-    cx.dld4(1, phys(k), ec[i]);
-    cx.dld4(2, phys(k), &os[i][1]);  // harmonics k+1, k+2
-    cx.dld4(3, phys(k), &es[i][1]);
-  }
+    for (int i = 0; i < NI; ++i) {
+      const int k = r * (Q / 4) + 2 * (tid + (g * NI + i) * NT);
+      cx.dld4(0, phys(k), oc[i]);
+      cx.dld4(1, phys(k), ec[i]);
+      cx.dld4(2, phys(k), &os[i][1]);  // harmonics k+1, k+2
+      cx.dld4(3, phys(k), &es[i][1]);
+    }
 #pragma unroll
-  for (int i = 0; i < NI; ++i) {
-    const int k = r * (Q / 4) + 2 * (tid + i * NT);
-    float2 po = cx.shfl_up(os[i][2], 1), pe = cx.shfl_up(es[i][2], 1);
-    if ((tid & 31) == 0) {  // harmonic k (position k - 1) of lane 0
-      po = k > 0 ? cx.dld2(2, phys(k - 1)) : make_float2(0.f, 0.f);
-      pe = k > 0 ? cx.dld2(3, phys(k - 1)) : make_float2(0.f, 0.f);
+    for (int i = 0; i < NI; ++i) {
+      const int k = r * (Q / 4) + 2 * (tid + (g * NI + i) * NT);
+      float2 po = cx.shfl_up(os[i][2], 1), pe = cx.shfl_up(es[i][2], 1);
+      if ((tid & 31) == 0) {  // harmonic k (position k - 1) of lane 0
+        po = k > 0 ? cx.dld2(2, phys(k - 1)) : make_float2(0.f, 0.f);
+        pe = k > 0 ? cx.dld2(3, phys(k - 1)) : make_float2(0.f, 0.f);
+      }
+      os[i][0] = po;
+      es[i][0] = pe;
     }
-    os[i][0] = po;
-    es[i][0] = pe;
-  }
 #pragma unroll
-  for (int i = 0; i < NI; ++i) {
-    const int k = r * (Q / 4) + 2 * (tid + i * NT);
-    float2 X0[2], XM[2], XH[2], XN[2];  // X(k+j), X(N-k-j), X(N/2-k-j), X(N/2+k+j)
+    for (int i = 0; i < NI; ++i) {
+      const int k = r * (Q / 4) + 2 * (tid + (g * NI + i) * NT);
+      float2 X0[2], XM[2], XH[2], XN[2];  // X(k+j), X(N-k-j), X(N/2-k-j), X(N/2+k+j)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const float2 ck = add2(ec[i][j], oc[i][j]), cm = sub2(ec[i][j], oc[i][j]);
-      const float2 sk = add2(os[i][j], es[i][j]), sm = sub2(os[i][j], es[i][j]);
-      X0[j] = make_float2(ck.x + sk.y, (ck.y - sk.x) * cj);
-      XM[j] = make_float2(ck.x - sk.y, (ck.y + sk.x) * cj);
-      XH[j] = make_float2(cm.x + sm.y, (cm.y - sm.x) * cj);
-      XN[j] = make_float2(cm.x - sm.y, (cm.y + sm.x) * cj);
+      for (int j = 0; j < 2; ++j) {
+        const float2 ck = add2(ec[i][j], oc[i][j]), cm = sub2(ec[i][j], oc[i][j]);
+        const float2 sk = add2(os[i][j], es[i][j]), sm = sub2(os[i][j], es[i][j]);
+        X0[j] = make_float2(ck.x + sk.y, (ck.y - sk.x) * cj);
+        XM[j] = make_float2(ck.x - sk.y, (ck.y + sk.x) * cj);
+        XH[j] = make_float2(cm.x + sm.y, (cm.y - sm.x) * cj);
+        XN[j] = make_float2(cm.x - sm.y, (cm.y + sm.x) * cj);
+      }
+      if (k == 0) {  // X(0) = C(0), X(N/2) = C(N/2): the DST has no harmonic 0
+        const float2 ck = add2(ec[i][0], oc[i][0]), cm = sub2(ec[i][0], oc[i][0]);
+        X0[0] = make_float2(ck.x, ck.y * cj);
+        XN[0] = make_float2(cm.x, cm.y * cj);
+      }
+      cx.stg4(xo + k, make_float4(X0[0].x, X0[0].y, X0[1].x, X0[1].y));
+      cx.stg4(xo + (N / 2 + k), make_float4(XN[0].x, XN[0].y, XN[1].x, XN[1].y));
+      if (k > 0) {
+        cx.stg2(xo + (N - k), XM[0]);
+        cx.stg2(xo + (N / 2 - k), XH[0]);
+      }
+      cx.stg2(xo + (N - k - 1), XM[1]);
+      cx.stg2(xo + (N / 2 - k - 1), XH[1]);
     }
-    if (k == 0) {  // X(0) = C(0), X(N/2) = C(N/2): the DST has no harmonic 0
-      const float2 ck = add2(ec[i][0], oc[i][0]), cm = sub2(ec[i][0], oc[i][0]);
-      X0[0] = make_float2(ck.x, ck.y * cj);
-      XN[0] = make_float2(cm.x, cm.y * cj);
-    }
-    cx.stg4(xo + k, make_float4(X0[0].x, X0[0].y, X0[1].x, X0[1].y));
-    cx.stg4(xo + (N / 2 + k), make_float4(XN[0].x, XN[0].y, XN[1].x, XN[1].y));
-    if (k > 0) {
-      cx.stg2(xo + (N - k), XM[0]);
-      cx.stg2(xo + (N / 2 - k), XH[0]);
-    }
-    cx.stg2(xo + (N - k - 1), XM[1]);
-    cx.stg2(xo + (N / 2 - k - 1), XH[1]);
   }
   if (r == 0 && tid == 0) {
     const float2 cq = cx.dld2(1, phys(Q)), sq = cx.dld2(2, phys(Q - 1));  // C(N/4) = E(N/4), S(N/4) = O(N/4)

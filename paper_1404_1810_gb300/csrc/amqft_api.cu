@@ -408,7 +408,7 @@ static int exec_n(amqft_plan_t p, long long batch, const void* in, void* out, in
     ++p->launches;
     return AMQFT_OK;
   }
-  if (paired_supported(p->log2n, p->variant, p->dtype) && !((a0 | b0) & 15u)) {
+  if (paired_supported(p->log2n, p->variant, p->dtype, batch) && !((a0 | b0) & 15u)) {
     e = paired_launch(p->log2n, in, out, batch, inverse, p->d_ctab, p->small, st);
     if (e != cudaSuccess) return cuda_fail(e, "paired kernel launch");
     ++p->launches;

@@ -60,9 +60,10 @@ cudaError_t multipass_variant_4(const MpArgs&, float*, float*, const SmallConsts
 cudaError_t multipass_variant_6(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t, long long* nlaunch);
 cudaError_t multipass_variant_8(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t, long long* nlaunch);
 
-// paired-region kernel (N = 2^14 .. 2^16, variant 4, complex64): one transform
-// per cluster of four CTAs, persistent over the batch; in and out 16-byte aligned
-bool paired_supported(int logN, int variant, int dtype);
+// paired-region kernel (N = 2^14 .. 2^16, variant 4, complex64, batch below
+// 2^31): one transform per cluster of four CTAs, persistent over the batch;
+// in and out 16-byte aligned
+bool paired_supported(int logN, int variant, int dtype, long long batch);
 cudaError_t paired_launch(int logN, const void* in, void* out, long long batch, int inverse, const float* ctab,
                           const SmallConsts& K, cudaStream_t st);
 cudaError_t paired_launch_14(const void*, void*, long long, int, const float*, const SmallConsts&, cudaStream_t);

@@ -4,8 +4,8 @@
 
 namespace amqft {
 
-bool paired_supported(int logN, int variant, int dtype) {
-  return variant == 4 && dtype == AMQFT_C64 && logN >= 14 && logN <= 16;
+bool paired_supported(int logN, int variant, int dtype, long long batch) {
+  return variant == 4 && dtype == AMQFT_C64 && logN >= 14 && logN <= 16 && batch <= 0x7fffffffLL;
 }
 
 cudaError_t paired_launch(int logN, const void* in, void* out, long long batch, int inverse, const float* ctab,

@@ -876,12 +876,13 @@ PR_HD constexpr int smem_bytes() {
   return region_f2<T>() * 8 + ((1 << T) - 32) * 4;
 }
 
-// The cluster's work: transforms cid, cid + ncl, ... of the batch.
+// The cluster's work: transforms cid, cid + ncl, ... of the batch (batch below
+// 2^31; the dispatch checks it).
 // reg: this CTA's region; Ctx reaches CTA q's region with dst2 / dld2 / dld4
 // (float2 index into the region: distributed shared memory for the others).
 template <int LN, bool INV, class Ctx>
-PR_HD void paired_body(Ctx& cx, const float2* __restrict__ in, float2* __restrict__ out, long long batch,
-                       long long cid, long long ncl, float2* reg, float* __restrict__ cst,
+PR_HD void paired_body(Ctx& cx, const float2* __restrict__ in, float2* __restrict__ out, int batch, int cid,
+                       int ncl, float2* reg, float* __restrict__ cst,
                        const float* __restrict__ ctab, const LeafConsts& K) {
   constexpr int T = LN - 2, NT = 1 << (T - 5);
   constexpr long long N = 1LL << LN;
@@ -889,9 +890,9 @@ PR_HD void paired_body(Ctx& cx, const float2* __restrict__ in, float2* __restric
   const int ncst = (r & 1) == 0 ? (1 << T) - 32 : (1 << (T - 1)) - 32;
   for (int i = tid; i < ncst; i += NT) cst[i] = ctab[30 + i];
   LoadRound<LN> R;
-  if (cid < batch) load_fetch<LN>(cx, in + cid * N, r, 0, R);
-  for (long long t = cid; t < batch; t += ncl) {
-    const float2* xin = in + t * N;
+  if (cid < batch) load_fetch<LN>(cx, in + (long long)cid * N, r, 0, R);
+  for (int t = cid; t < batch; t += ncl) {
+    const float2* xin = in + (long long)t * N;
     cx.sync_cluster();  // the previous store has read every region
     load_scatter<LN, INV>(cx, r, 0, R);
 #pragma unroll
@@ -908,9 +909,9 @@ PR_HD void paired_body(Ctx& cx, const float2* __restrict__ in, float2* __restric
       default: cta_transform<T, 1, false>(cx, reg, cst, K); break;
     }
     cx.sync_cluster();
-    store_stage<LN, INV>(cx, out + t * N, r);
+    store_stage<LN, INV>(cx, out + (long long)t * N, r);
     // the next transform's first reads fly across the barrier at the loop top
-    if (t + ncl < batch) load_fetch<LN>(cx, in + (t + ncl) * N, r, 0, R);
+    if (t + ncl < batch) load_fetch<LN>(cx, in + (long long)(t + ncl) * N, r, 0, R);
   }
   cx.sync_cluster();  // keep the regions alive for the other CTAs' reads
 }

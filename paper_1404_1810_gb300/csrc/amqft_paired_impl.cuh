@@ -11,8 +11,14 @@ namespace pr {
 
 struct DevCtx {
   int tid, rank;
-  unsigned lbase;     // shared-window address of this CTA's region
-  unsigned cbase[4];  // shared::cluster addresses of the four regions
+  unsigned lbase;  // shared-window address of this CTA's region
+  // shared::cluster address of CTA q's region (mapa, recomputed at each use
+  // rather than held in four registers through the whole transform)
+  __device__ __forceinline__ unsigned cbase(int q) const {
+    unsigned a;
+    asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(lbase), "r"(q));
+    return a;
+  }
   __device__ __forceinline__ void sync_warp() { __syncwarp(); }
   __device__ __forceinline__ void sync_cta() { __syncthreads(); }
   __device__ __forceinline__ void sync_cluster() { cg::this_cluster().sync(); }
@@ -29,7 +35,7 @@ struct DevCtx {
     if (q == rank)
       asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(lbase + 8u * (unsigned)i), "f"(v.x), "f"(v.y) : "memory");
     else
-      asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(cbase[q] + 8u * (unsigned)i), "f"(v.x), "f"(v.y)
+      asm volatile("st.shared::cluster.v2.f32 [%0], {%1, %2};" ::"r"(cbase(q) + 8u * (unsigned)i), "f"(v.x), "f"(v.y)
                    : "memory");
   }
   __device__ __forceinline__ float2 dld2(int q, int i) {
@@ -37,7 +43,7 @@ struct DevCtx {
     if (q == rank)
       asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(lbase + 8u * (unsigned)i) : "memory");
     else
-      asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(cbase[q] + 8u * (unsigned)i)
+      asm volatile("ld.shared::cluster.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(cbase(q) + 8u * (unsigned)i)
                    : "memory");
     return v;
   }
@@ -49,7 +55,7 @@ struct DevCtx {
                    : "r"(lbase + 8u * (unsigned)i) : "memory");
     else
       asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(a), "=f"(b), "=f"(c), "=f"(d)
-                   : "r"(cbase[q] + 8u * (unsigned)i) : "memory");
+                   : "r"(cbase(q) + 8u * (unsigned)i) : "memory");
     v[0] = make_float2(a, b);
     v[1] = make_float2(c, d);
   }
@@ -70,11 +76,8 @@ __global__ void __launch_bounds__(paired_tpb(LN), paired_ctas(LN))
   cx.tid = (int)threadIdx.x;
   cx.rank = (int)cl.block_rank();
   cx.lbase = (unsigned)__cvta_generic_to_shared(psm);
-#pragma unroll
-  for (int q = 0; q < 4; ++q)
-    asm("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(cx.cbase[q]) : "r"(cx.lbase), "r"(q));
   float* cst = reinterpret_cast<float*>(psm + region_f2<T>());
-  paired_body<LN, INV>(cx, in, out, batch, (long long)(blockIdx.x >> 2), (long long)(gridDim.x >> 2), psm, cst,
+  paired_body<LN, INV>(cx, in, out, (int)batch, (int)(blockIdx.x >> 2), (int)(gridDim.x >> 2), psm, cst,
                        ctab, K);
 }
 

@@ -496,52 +496,6 @@ PR_HD void run_tail(float2* __restrict__ blk, const LeafConsts& K) {
   for (int e = 0; e < SZ; ++e) blk[phys(992 + e)] = t[e];
 }
 
-// ---------------------------------------------------------------------
-// one chain level, in place: the tree of 2^m values at [P, P + 2^m) and the
-// chain below at [P + 2^m, ...), P = top - 2^(m+1) (top: the chain's end,
-// position N/4 of the rest region, or 1024 of the last block); item k covers
-// S at k, 2^(m+1) - k, 2^m - k, 2^m + k.  Items k0, k0 + step, ...
-// ---------------------------------------------------------------------
-template <int CX>
-PR_HD void chain_level(float2* __restrict__ sm, int P, int m, int k0, int step) {
-  const int H = 1 << m;
-  if (CX == 0) {
-    for (int k = k0; k <= H / 2; k += step) {
-      if (k == 0) {
-        const float2 o = sm[phys(P)], e = sm[phys(P + H)], eH = sm[phys(P + 2 * H)];
-        sm[phys(P)] = add2(e, o);
-        sm[phys(P + 2 * H)] = sub2(e, o);
-        sm[phys(P + H)] = eH;
-      } else if (k == H / 2) {
-        const float2 o = sm[phys(P + k)], e = sm[phys(P + H + k)];
-        sm[phys(P + k)] = add2(e, o);
-        sm[phys(P + 2 * H - k)] = sub2(e, o);
-      } else {
-        const float2 o1 = sm[phys(P + k)], e1 = sm[phys(P + H + k)];
-        const float2 o2 = sm[phys(P + H - k)], e2 = sm[phys(P + 2 * H - k)];
-        sm[phys(P + k)] = add2(e1, o1);
-        sm[phys(P + 2 * H - k)] = sub2(e1, o1);
-        sm[phys(P + H - k)] = add2(e2, o2);
-        sm[phys(P + H + k)] = sub2(e2, o2);
-      }
-    }
-  } else {
-    for (int k = k0 + 1; k <= H / 2; k += step) {
-      if (k == H / 2) {
-        const float2 o = sm[phys(P + k - 1)], e = sm[phys(P + H + k - 1)];
-        sm[phys(P + k - 1)] = add2(o, e);
-        sm[phys(P + 2 * H - k - 1)] = sub2(o, e);
-      } else {
-        const float2 o1 = sm[phys(P + k - 1)], e1 = sm[phys(P + H + k - 1)];
-        const float2 o2 = sm[phys(P + H - k - 1)], e2 = sm[phys(P + 2 * H - k - 1)];
-        sm[phys(P + k - 1)] = add2(o1, e1);
-        sm[phys(P + 2 * H - k - 1)] = sub2(o1, e1);
-        sm[phys(P + H - k - 1)] = add2(o2, e2);
-        sm[phys(P + H + k - 1)] = sub2(o2, e2);
-      }
-    }
-  }
-}
 
 // ---------------------------------------------------------------------
 // chain levels of a rest CTA.  Level m's item k (H = 2^m) reads E(k), E(H-k)
@@ -576,17 +530,18 @@ PR_HD void chain_item(float2* __restrict__ sm, int P, int H, int k) {
   sm[phys(P + H + k - d)] = CX == 0 ? sub2(e2, o2) : sub2(o2, e2);
 }
 
-// One chain level of a rest CTA with every item's reads issued before its
-// writes: item k = tid + i NT (i < H/(2 NT)) and, for thread 0, item H/2.
-// The items of a level are disjoint, so a level needs no barrier inside.
-template <int T, int CX, int m>
-PR_HD void chain_level_cta(float2* __restrict__ sm, int tid) {
-  constexpr int H = 1 << m, P = (1 << T) - 2 * H, NT = 1 << (T - 5), NI = H / 2 / NT, d = CX;
+// One chain level m on a group of NTH threads (thread tid), the chain ending at
+// position TOP of sm: item k = tid + i NTH, every item's reads issued before
+// its writes; item H/2 (and item 0) by thread 0.  The items of a level are
+// disjoint, so a level needs no barrier inside.
+template <int CX, int m, int NTH, int TOP>
+PR_HD void chain_single(float2* __restrict__ sm, int tid) {
+  constexpr int H = 1 << m, P = TOP - 2 * H, NI = (H / 2 + NTH - 1) / NTH, d = CX;
   float2 o1[NI], e1[NI], o2[NI], e2[NI];
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
-    const int k = tid + i * NT;
-    if (CX == 1 && k == 0) {  // the DST has no item 0 (its positions would start at P - 1)
+    const int k = tid + i * NTH;
+    if ((CX == 1 && k == 0) || k >= H / 2) {  // no DST item 0 (its positions would start at P - 1)
       o1[i] = e1[i] = o2[i] = e2[i] = make_float2(0.f, 0.f);
       continue;
     }
@@ -599,7 +554,8 @@ PR_HD void chain_level_cta(float2* __restrict__ sm, int tid) {
   if (CX == 0 && tid == 0) eH = sm[phys(P + 2 * H)];
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
-    const int k = tid + i * NT;
+    const int k = tid + i * NTH;
+    if (k >= H / 2) continue;
     if (k == 0) {
       if (CX == 0) {  // S(0) = E(0) + O(0), S(2H) = E(0) - O(0), S(H) = E(H)
         sm[phys(P)] = add2(e1[i], o1[i]);
@@ -614,6 +570,56 @@ PR_HD void chain_level_cta(float2* __restrict__ sm, int tid) {
     sm[phys(P + H + k - d)] = CX == 0 ? sub2(e2[i], o2[i]) : sub2(o2[i], e2[i]);
   }
   if (tid == 0) chain_item<CX>(sm, P, H, H / 2);
+}
+
+// Chain levels m and m+1 in one pass.  Level m's item k (0 < k < H/2)
+// gives S at k, 2H-k (the inputs of level m+1's item k) and at H-k, H+k (those
+// of item H-k), so the three items form a closed orbit: its eight tree values
+// and two chain values are read, and its eight outputs of level m+1 written,
+// by one thread, and no other thread touches those positions.  The orbits of
+// items 0 and H/2 (which meet the fixed points of the next level) are run by
+// thread 0 item by item, in place.
+template <int CX, int m, int NTH, int TOP>
+PR_HD void chain_pair(float2* __restrict__ sm, int tid) {
+  constexpr int H = 1 << m, P = TOP - 2 * H, H2 = 2 * H, P2 = TOP - 2 * H2, d = CX;
+  constexpr int NI = (H / 2 + NTH - 1) / NTH;
+  // one orbit at a time (its positions are its own, so no order is needed
+  // between orbits; this keeps the register footprint at one orbit)
+#pragma unroll
+  for (int i = 0; i < NI; ++i) {
+    const int k = tid + i * NTH;
+    if (k == 0 || k >= H / 2) continue;
+    const float2 ea = sm[phys(P + H + k - d)];      // E(k)
+    const float2 eb = sm[phys(P + 2 * H - k - d)];  // E(H-k)
+    const float2 oa = sm[phys(P + k - d)];          // O(k)
+    const float2 ob = sm[phys(P + H - k - d)];      // O(H-k)
+    const float2 p0 = sm[phys(P2 + k - d)];         // O'(k)
+    const float2 p1 = sm[phys(P2 + H2 - k - d)];    // O'(2H-k)
+    const float2 p2 = sm[phys(P2 + H - k - d)];     // O'(H-k)
+    const float2 p3 = sm[phys(P2 + H + k - d)];     // O'(H+k)
+    // level m: DCT S = E +- O, DST S = O +- E
+    const float2 sk = CX == 0 ? add2(ea, oa) : add2(oa, ea);   // S(k)
+    const float2 s2 = CX == 0 ? sub2(ea, oa) : sub2(oa, ea);   // S(2H-k)
+    const float2 sh = CX == 0 ? add2(eb, ob) : add2(ob, eb);   // S(H-k)
+    const float2 sp = CX == 0 ? sub2(eb, ob) : sub2(ob, eb);   // S(H+k)
+    // level m+1, item k: E'(k) = S(k), E'(2H-k) = S(2H-k)
+    sm[phys(P2 + k - d)] = CX == 0 ? add2(sk, p0) : add2(p0, sk);
+    sm[phys(P2 + 2 * H2 - k - d)] = CX == 0 ? sub2(sk, p0) : sub2(p0, sk);
+    sm[phys(P2 + H2 - k - d)] = CX == 0 ? add2(s2, p1) : add2(p1, s2);
+    sm[phys(P2 + H2 + k - d)] = CX == 0 ? sub2(s2, p1) : sub2(p1, s2);
+    // level m+1, item H-k: E'(H-k) = S(H-k), E'(H+k) = S(H+k)
+    sm[phys(P2 + H - k - d)] = CX == 0 ? add2(sh, p2) : add2(p2, sh);
+    sm[phys(P2 + 2 * H2 - H + k - d)] = CX == 0 ? sub2(sh, p2) : sub2(p2, sh);
+    sm[phys(P2 + H + k - d)] = CX == 0 ? add2(sp, p3) : add2(p3, sp);
+    sm[phys(P2 + H2 + H - k - d)] = CX == 0 ? sub2(sp, p3) : sub2(p3, sp);
+  }
+  if (tid == 0) {
+    chain_item<CX>(sm, P, H, 0);
+    chain_item<CX>(sm, P, H, H / 2);
+    chain_item<CX>(sm, P2, H2, 0);
+    chain_item<CX>(sm, P2, H2, H);
+    chain_item<CX>(sm, P2, H2, H / 2);
+  }
 }
 
 // ---------------------------------------------------------------------
@@ -642,11 +648,18 @@ PR_HD void block_leaf(float2* __restrict__ blk, int ln, const LeafConsts& K) {
   st_run<32>(blk, 32 * ln, x);
 }
 
-// chain levels 5 .. MTOP inside the last block (lanes of one warp, warp
-// synchronisation between levels is the caller's: this runs one level)
-template <int CX>
-PR_HD void block_chain_level(float2* __restrict__ blk, int m, int ln) {
-  chain_level<CX>(blk, 1024 - (2 << m), m, ln, 32);
+// chain levels m .. T-5 inside the last block (the 32 lanes of its warp), two
+// levels a pass
+template <int T, int CX, int m, class Ctx>
+PR_HD void block_chain(Ctx& cx, float2* __restrict__ blk, int ln) {
+  if constexpr (m + 1 <= T - 5) {
+    cx.sync_warp();
+    chain_pair<CX, m, 32, 1024>(blk, ln);
+    block_chain<T, CX, m + 2>(cx, blk, ln);
+  } else if constexpr (m == T - 5) {
+    cx.sync_warp();
+    chain_single<CX, m, 32, 1024>(blk, ln);
+  }
 }
 
 // ---------------------------------------------------------------------
@@ -671,10 +684,7 @@ PR_HD void block_stage(Ctx& cx, float2* __restrict__ blk, int ln, const float* _
   freq_write<5, 5, 0, VIRT>(blk, 0, ln, x);
   if constexpr (VIRT) {
     // chain levels of the trees of 32 .. 2^(T-5) values inside the block
-    for (int m = 5; m <= T - 5; ++m) {
-      cx.sync_warp();
-      block_chain_level<CX>(blk, m, ln);
-    }
+    block_chain<T, CX, 5>(cx, blk, ln);
   }
 }
 
@@ -710,13 +720,9 @@ PR_HD void cta_transform(Ctx& cx, float2* __restrict__ reg, const float* __restr
   if constexpr (!TOP) {
     // chain levels of the trees of 2^(T-4) .. 2^(T-1) values
     cx.sync_cta();
-    chain_level_cta<T, CX, T - 4>(reg, tid);
+    chain_pair<CX, T - 4, (1 << (T - 5)), (1 << T)>(reg, tid);
     cx.sync_cta();
-    chain_level_cta<T, CX, T - 3>(reg, tid);
-    cx.sync_cta();
-    chain_level_cta<T, CX, T - 2>(reg, tid);
-    cx.sync_cta();
-    chain_level_cta<T, CX, T - 1>(reg, tid);
+    chain_pair<CX, T - 2, (1 << (T - 5)), (1 << T)>(reg, tid);
   }
 }
 

@@ -64,15 +64,14 @@ typedef struct amqft_plan_s *amqft_plan_t;
  * M/8 constants 2cos, 1/(2cos), 2sin or 1/(2sin) of theta*(2j+1) for every
  * periodisation M = 16..N, N/4 - 2 floats in all) on the current device.
  * Lengths up to 2^AMQFT_LOG2N_FUSED_MAX run in one fused kernel (one HBM
- * read and write per sample).  Longer transforms (variants 2, 4, 6, 8 only:
- * the others contain recurrences) run as several passes over a workspace the
- * plan allocates: two buffers of the transform's size per transform of a
+ * read and write per sample).  Longer transforms (every variant; the
+ * recurrences of variants 1, 3, 5, 7 become chunk passes and a scan of the
+ * chunk totals) run as several passes over a workspace the plan allocates: two buffers of the transform's size per transform of a
  * chunk, at most 2 GiB, the batch processed chunk by chunk.  That workspace
  * (like the staging of amqft_exec_host) belongs to the plan, so the exec calls
  * of one plan must be ordered: one stream, or streams joined by events.  Calls
  * on different plans are independent.
- * Errors: AMQFT_ERR_N (log2n < 0 or > AMQFT_LOG2N_MAX), AMQFT_ERR_VARIANT
- * (also variants 1, 3, 5, 7 with log2n > AMQFT_LOG2N_FUSED_MAX),
+ * Errors: AMQFT_ERR_N (log2n < 0 or > AMQFT_LOG2N_MAX), AMQFT_ERR_VARIANT (not in 1..8),
  * AMQFT_ERR_DTYPE (not an amqft_dtype), AMQFT_ERR_ARG (out NULL or batch < 0), AMQFT_ERR_DEVICE,
  * AMQFT_ERR_NOMEM, AMQFT_ERR_CUDA.  On error *out is set to NULL. */
 int amqft_plan(amqft_plan_t *out, int log2n, int variant, int64_t batch, int dtype);

@@ -97,13 +97,18 @@ __global__ void ragged_bucket_kernel(const unsigned char* __restrict__ log2n, co
 }
 
 
-static cudaError_t multipass_launch(int variant, const MpArgs& a, float* W0, float* W1, const SmallConsts& K,
-                                    cudaStream_t st, long long* nl) {
+cudaError_t multipass_dispatch(int variant, const MpArgs& a, float* W0, float* W1, const SmallConsts& K,
+                               cudaStream_t st, long long* nl) {
   switch (variant) {
+    case 1: return multipass_variant_1(a, W0, W1, K, st, nl);
     case 2: return multipass_variant_2(a, W0, W1, K, st, nl);
+    case 3: return multipass_variant_3(a, W0, W1, K, st, nl);
     case 4: return multipass_variant_4(a, W0, W1, K, st, nl);
+    case 5: return multipass_variant_5(a, W0, W1, K, st, nl);
     case 6: return multipass_variant_6(a, W0, W1, K, st, nl);
-    default: return multipass_variant_8(a, W0, W1, K, st, nl);
+    case 7: return multipass_variant_7(a, W0, W1, K, st, nl);
+    case 8: return multipass_variant_8(a, W0, W1, K, st, nl);
+    default: return cudaErrorInvalidValue;
   }
 }
 
@@ -274,10 +279,6 @@ int amqft_plan(amqft_plan_t* out, int log2n, int variant, int64_t batch, int dty
   if (log2n < 0 || log2n > AMQFT_LOG2N_MAX)
     return fail(AMQFT_ERR_N, "amqft_plan: log2n=%d outside [0, %d]", log2n, AMQFT_LOG2N_MAX);
   if (variant < 1 || variant > 8) return fail(AMQFT_ERR_VARIANT, "amqft_plan: variant=%d not in 1..8", variant);
-  if (log2n > AMQFT_LOG2N_FUSED_MAX && (variant & 1))
-    return fail(AMQFT_ERR_VARIANT,
-                "amqft_plan: variant %d (a recurrence variant) is limited to log2n <= %d; "
-                "variants 2, 4, 6, 8 reach %d", variant, AMQFT_LOG2N_FUSED_MAX, AMQFT_LOG2N_MAX);
   if (dtype != AMQFT_C64 && dtype != AMQFT_CBF16 && dtype != AMQFT_CF16)
     return fail(AMQFT_ERR_DTYPE, "amqft_plan: dtype=%d is not AMQFT_C64, AMQFT_CBF16 or AMQFT_CF16", dtype);
   if (batch < 0) return fail(AMQFT_ERR_ARG, "amqft_plan: batch=%lld < 0", (long long)batch);
@@ -392,7 +393,7 @@ static int exec_n(amqft_plan_t p, long long batch, const void* in, void* out, in
       a.toff = nullptr;
       a.ntdev = nullptr;
       long long nl = 0;
-      e = multipass_launch(p->variant, a, p->d_work, p->d_work + per_buf, p->small, st, &nl);
+      e = multipass_dispatch(p->variant, a, p->d_work, p->d_work + per_buf, p->small, st, &nl);
       p->launches += nl;
       if (e != cudaSuccess) return cuda_fail(e, "multi-pass launch");
     }
@@ -702,7 +703,7 @@ int amqft_exec_ragged(amqft_plan_t p, int64_t count, const int64_t* d_offsets, c
     m.toff = (const long long*)d_offsets;
     m.ntdev = p->d_rcnt + c;
     nl = 0;
-    e = multipass_launch(p->variant, m, p->d_rwork, p->d_rwork + capc * 4 * RSg, p->small, st, &nl);
+    e = multipass_dispatch(p->variant, m, p->d_rwork, p->d_rwork + capc * 4 * RSg, p->small, st, &nl);
     p->launches += nl;
     if (e != cudaSuccess) return cuda_fail(e, "ragged multi-pass launch");
   }

@@ -6,6 +6,10 @@ namespace amqft {
 cudaError_t launch_variant_5(const FusedArgs& a, const SmallConsts& K, const FusedConfig& c, cudaStream_t st) {
   return launch_v<5>(a, K, c, st);
 }
+cudaError_t multipass_variant_5(const MpArgs& a, float* W0, float* W1, const SmallConsts& K, cudaStream_t st,
+                                long long* nlaunch) {
+  return mp_run<5>(a, W0, W1, K, st, nlaunch);
+}
 cudaError_t ragged_variant_5(const FusedArgs& a, const SmallConsts& K, const RaggedArgs& r, const RaggedLaunch& L,
                                cudaStream_t st, long long* nlaunch) {
   return ragged_run<5>(a, K, r, L, st, nlaunch);

@@ -54,11 +54,19 @@ cudaError_t ragged_variant_7(const FusedArgs&, const SmallConsts&, const RaggedA
 cudaError_t ragged_variant_8(const FusedArgs&, const SmallConsts&, const RaggedArgs&, const RaggedLaunch&, cudaStream_t,
                              long long* nlaunch);
 
-// multi-pass path (2^17 <= N <= 2^24), variants 2, 4, 6, 8
+// multi-pass path (2^17 <= N <= 2^24), every variant
+cudaError_t multipass_variant_1(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t, long long* nlaunch);
 cudaError_t multipass_variant_2(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t, long long* nlaunch);
+cudaError_t multipass_variant_3(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t, long long* nlaunch);
 cudaError_t multipass_variant_4(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t, long long* nlaunch);
+cudaError_t multipass_variant_5(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t, long long* nlaunch);
 cudaError_t multipass_variant_6(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t, long long* nlaunch);
+cudaError_t multipass_variant_7(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t, long long* nlaunch);
 cudaError_t multipass_variant_8(const MpArgs&, float*, float*, const SmallConsts&, cudaStream_t, long long* nlaunch);
+// the whole multi-pass sequence of one chunk for `variant` (W0, W1: the two
+// workspace buffers; nlaunch counts the kernels launched)
+cudaError_t multipass_dispatch(int variant, const MpArgs& a, float* W0, float* W1, const SmallConsts& K,
+                               cudaStream_t st, long long* nlaunch);
 
 // paired-region kernel (N = 2^14 .. 2^16, variant 4, complex64, batch below
 // 2^31): one transform per cluster of four CTAs, persistent over the batch;

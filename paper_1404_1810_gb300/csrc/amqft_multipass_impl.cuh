@@ -6,16 +6,20 @@
 //            scattered into the regions;
 //   levels   tree levels of node size > S in bands of up to four levels per
 //            pass (the fused kernel's fold and chunk bands, in place in the
-//            workspace), the M2/M6 time phase one level per pass in gather
-//            form, and chain levels of periodisation > 4S one per pass;
+//            workspace), the M2/M4/M6/M8 neighbour phase one level per pass in
+//            gather form, the M1/M3/M5/M7 recurrences one level per three
+//            passes (chunk totals, a scan of the totals per node, the chunks
+//            re-run with their carries), and chain levels of periodisation
+//            > 4S one per pass;
 //   solve    one CTA per pair of tree nodes of size S (node mode) and one per
 //            region tail (the trees of size <= S plus the chain up to 4S, a
 //            region of N' = 4S) in shared memory, with the fused kernel's
 //            bands, register subtrees and passes;
 //   store    last chain level (time-first variants), D_r^F and D_c^F.
 //
-// Variants 2, 4, 6 and 8 only: the recurrences of 1, 3, 5 and 7 would need a
-// grid-wide scan per level.
+// The recurrence variants (1, 3, 5, 7) take the scans without any wait
+// between CTAs: a level is three launches, so every carry a chunk needs has
+// been written by an earlier kernel of the stream.
 #pragma once
 
 #include "amqft_bands.cuh"
@@ -197,6 +201,153 @@ __global__ void mp_neighbour_kernel(MpArgs a, const float* __restrict__ Win, flo
   }
 }
 
+// Recurrence form of M_v on the B halves at node size 2^logLp > S: the
+// frequency phase of M1/M5 (ot variants, the first value halved) or the time
+// phase of M3/M7 (to variants, the last value halved), Tab. 5-6.  A node's B
+// half holds H = 2^(logLp-1) values in bit-reversed order; it is cut into SC
+// chunks of MP_RC values consecutive in recurrence order.  Viewed as MP_RC
+// rows of SC words, a chunk is one column: value e of the chunk in column col
+// lies at base + brev(e) * SC + col (prefix recurrence, k = brev(col)) or at
+// base + brev(MP_RC - 1 - e) * SC + col (suffix recurrence, k = SC - 1 -
+// brev(col)), so the 32 columns of a warp are 32 consecutive words.
+// Each recurrence y(m) = x(m) + y(m-1) (M5/M7) or x(m) - y(m-1) (M1/M3) is
+// run per chunk from a zero carry; with an even chunk length the carry into
+// chunk k is the plain sum of the earlier chunks' last values, added
+// (alternating sign for M1/M3) when the chunk is run again.
+constexpr int MP_RLOG_C = 5;
+constexpr int MP_RC = 1 << MP_RLOG_C;  // values per chunk (even)
+
+template <int V>
+__device__ __forceinline__ bool rec_prefix(int ctx) {
+  if constexpr (V == 1) return ctx == 0;
+  else if constexpr (V == 5) return ctx == 1;
+  else if constexpr (V == 3) return ctx == 1;
+  else return ctx == 0;  // V == 7
+}
+
+struct RecChunk {
+  float* R;      // the region
+  long long nd;  // node index over the chunk's regions
+  int base;      // first position of the node's B half
+  int col, k, logSC;
+  bool prefix;
+  __device__ __forceinline__ int pos(int e) const {
+    return base + (brev(prefix ? e : MP_RC - 1 - e, MP_RLOG_C) << logSC) + col;
+  }
+};
+
+// class-0 nodes of size 2^logLp per region, and the chunks of a node
+__device__ __forceinline__ long long rec_nodes(const MpArgs& a, int logLp) {
+  return (1LL << (a.logN - 1 - logLp)) - 1;
+}
+
+template <int V>
+__device__ __forceinline__ RecChunk rec_chunk(const MpArgs& a, float* W, int logLp, long long w) {
+  const int half = 1 << (a.logN - 1), H = 1 << (logLp - 1);
+  RecChunk c;
+  c.logSC = logLp - 1 - MP_RLOG_C;
+  const int SC = 1 << c.logSC;
+  const long long nb = rec_nodes(a, logLp);
+  c.nd = w >> c.logSC;
+  c.col = (int)(w & (SC - 1));
+  const long long rr = c.nd / nb;
+  const int p0 = (int)(c.nd - rr * nb) << logLp;
+  const int ctx = node_ctx<V>(p0, logLp, half, (int)(rr & 1));
+  c.R = W + rr * a.RSg;
+  c.base = ctx == 0 ? p0 + H : p0;
+  c.prefix = rec_prefix<V>(ctx);
+  const int bc = brev(c.col, c.logSC);
+  c.k = c.prefix ? bc : SC - 1 - bc;
+  return c;
+}
+
+// pass 1: every chunk from a zero carry; T[node * SC + k] = its last value
+template <int V>
+__global__ void mp_rec_total_kernel(MpArgs a, float* W, float* __restrict__ T, int logLp) {
+  constexpr bool hstart = Var<V>::ot;
+  constexpr bool alt = (V == 1 || V == 3);
+  const long long total = (4 * mp_nt(a) * rec_nodes(a, logLp)) << (logLp - 1 - MP_RLOG_C);
+  for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
+    const RecChunk c = rec_chunk<V>(a, W, logLp, w);
+    float x[MP_RC];
+#pragma unroll
+    for (int e = 0; e < MP_RC; ++e) x[e] = c.R[sw(c.pos(e))];
+    float prev = 0.f;
+#pragma unroll
+    for (int e = 0; e < MP_RC; ++e) {
+      float y;
+      if (hstart && c.k == 0 && e == 0) y = 0.5f * x[e];
+      else y = alt ? (x[e] - prev) : (x[e] + prev);
+      prev = y;
+    }
+    T[(c.nd << c.logSC) + c.k] = prev;
+  }
+}
+
+// pass 2: exclusive prefix sum of each node's SC chunk totals (SC >= 256),
+// one 256-thread CTA per node
+template <int V>
+__global__ void __launch_bounds__(256) mp_rec_scan_kernel(MpArgs a, float* T, int logLp) {
+  __shared__ float wsum[8];
+  const int logSC = logLp - 1 - MP_RLOG_C, per = (1 << logSC) >> 8;
+  const long long nodes = 4 * mp_nt(a) * rec_nodes(a, logLp);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (long long nd = blockIdx.x; nd < nodes; nd += gridDim.x) {
+    float* t = T + (nd << logSC) + (long long)threadIdx.x * per;
+    float s = 0.f;
+    for (int j = 0; j < per; ++j) s = s + t[j];
+    float incl = s;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const float o = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl = incl + o;
+    }
+    float run = __shfl_up_sync(0xffffffffu, incl, 1);
+    if (lane == 0) run = 0.f;
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    float wp = 0.f;
+    for (int j = 0; j < warp; ++j) wp = wp + wsum[j];
+    run = wp + run;
+    for (int j = 0; j < per; ++j) {
+      const float v = t[j];
+      t[j] = run;
+      run = run + v;
+    }
+    __syncthreads();  // wsum is rewritten by the next node
+  }
+}
+
+// pass 3: every chunk again, with its carry c: y = l + c (M5/M7), l -/+ c for
+// even/odd e (M1/M3); the to variants halve the last value of the node
+template <int V>
+__global__ void mp_rec_apply_kernel(MpArgs a, float* W, const float* __restrict__ T, int logLp) {
+  constexpr bool hstart = Var<V>::ot;
+  constexpr bool alt = (V == 1 || V == 3);
+  const long long total = (4 * mp_nt(a) * rec_nodes(a, logLp)) << (logLp - 1 - MP_RLOG_C);
+  for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
+    const RecChunk c = rec_chunk<V>(a, W, logLp, w);
+    const int SC = 1 << c.logSC;
+    const float cy = T[(c.nd << c.logSC) + c.k];
+    float x[MP_RC];
+#pragma unroll
+    for (int e = 0; e < MP_RC; ++e) x[e] = c.R[sw(c.pos(e))];
+    float prev = 0.f;
+#pragma unroll
+    for (int e = 0; e < MP_RC; ++e) {
+      float l;
+      if (hstart && c.k == 0 && e == 0) l = 0.5f * x[e];
+      else l = alt ? (x[e] - prev) : (x[e] + prev);
+      prev = l;
+      float y;
+      if (alt) y = (e & 1) ? (l + cy) : (l - cy);
+      else y = l + cy;
+      if (!hstart && c.k == SC - 1 && e == MP_RC - 1) y = 0.5f * y;
+      c.R[sw(c.pos(e))] = y;
+    }
+  }
+}
+
 // One chain level of periodisation M = 2^logM, gather form: ot variants the
 // D_n frequency phase, to variants the D_k time phase (Sect. 6.9).
 template <int V>
@@ -302,13 +453,21 @@ __global__ void __launch_bounds__(TPB) mp_solve_kernel(MpArgs a, float* W, const
         run_leaf<V>(sm + r * RSn, p0, node_ctx_g<V>(g, p0, LOG_LEAF, ctx_of(g, r)), K);
       }
       __syncthreads();
-      for (int b = bp.nb - 1; b >= 0; --b) {
-        run_chunk_band_r<V, TPB>(sm, snap, g, bp.logL[b], bp.R[b]);
-        __syncthreads();
+      if constexpr (Var<V>::scan) {
+        for (int lp = LOG_LEAF + 1; lp <= MP_LOG_S; ++lp) {
+          pass_recurrence<V, TPB, 16>(sm, tot, wsum, g, lp);
+          __syncthreads();
+        }
+      } else {
+        for (int b = bp.nb - 1; b >= 0; --b) {
+          run_chunk_band_r<V, TPB>(sm, snap, g, bp.logL[b], bp.R[b]);
+          __syncthreads();
+        }
       }
     } else {
       for (int lp = MP_LOG_S; lp >= LOG_LEAF + 1; --lp) {
-        pass_neighbour<V, TPB, 16>(sm, g, lp);
+        if constexpr (Var<V>::scan) pass_recurrence<V, TPB, 16>(sm, tot, wsum, g, lp);
+        else pass_neighbour<V, TPB, 16>(sm, g, lp);
         __syncthreads();
       }
       for (int w = threadIdx.x; w < 2 * nleaf; w += TPB) {
@@ -351,9 +510,16 @@ __global__ void __launch_bounds__(TPB) mp_solve_kernel(MpArgs a, float* W, const
         else run_tail<V>(sm, ctx0, logNp, K);
       }
       __syncthreads();
-      for (int b = bp.nb - 1; b >= 0; --b) {
-        run_chunk_band_r<V, TPB>(sm, snap, g, bp.logL[b], bp.R[b]);
-        __syncthreads();
+      if constexpr (Var<V>::scan) {
+        for (int lp = LOG_LEAF + 1; lp <= logNp - 2; ++lp) {
+          pass_recurrence<V, TPB, 16>(sm, tot, wsum, g, lp);
+          __syncthreads();
+        }
+      } else {
+        for (int b = bp.nb - 1; b >= 0; --b) {
+          run_chunk_band_r<V, TPB>(sm, snap, g, bp.logL[b], bp.R[b]);
+          __syncthreads();
+        }
       }
       for (int lm = LOG_LEAF + 2; lm <= logNp; ++lm) {
         pass_chain<V, TPB, 32>(sm, g, lm);
@@ -367,7 +533,8 @@ __global__ void __launch_bounds__(TPB) mp_solve_kernel(MpArgs a, float* W, const
       if (threadIdx.x == 0) run_tail<V>(sm, ctx0, logNp, K);
       __syncthreads();
       for (int lp = logNp - 2; lp >= LOG_LEAF + 1; --lp) {
-        pass_neighbour<V, TPB, 16>(sm, g, lp);
+        if constexpr (Var<V>::scan) pass_recurrence<V, TPB, 16>(sm, tot, wsum, g, lp);
+        else pass_neighbour<V, TPB, 16>(sm, g, lp);
         __syncthreads();
       }
       for (int w = threadIdx.x; w < nleaf; w += TPB)
@@ -430,18 +597,34 @@ cudaError_t mp_run(const MpArgs& a0, float* W0, float* W1, const SmallConsts& K,
     }
     return launched();
   };
+  // the M_v relation at node size 2^lp > S: the neighbour form in gather
+  // form (a band would read its descendants bit-reversed, scattered across
+  // sectors), or the recurrence as three in-place passes with the chunk
+  // totals in the free ping-pong buffer
+  auto relation = [&](int lp) -> cudaError_t {
+    if constexpr (Var<V>::scan) {
+      const long long nodes = 4 * a.nt * ((1LL << (logN - 1 - lp)) - 1);
+      const long long chunks = nodes << (lp - 1 - MP_RLOG_C);
+      mp_rec_total_kernel<V><<<grid_for(chunks), threads, 0, st>>>(a, cur, oth, lp);
+      if ((e = launched()) != cudaSuccess) return e;
+      mp_rec_scan_kernel<V><<<(unsigned)(nodes < 152LL * 16 ? nodes : 152LL * 16), 256, 0, st>>>(a, oth, lp);
+      if ((e = launched()) != cudaSuccess) return e;
+      mp_rec_apply_kernel<V><<<grid_for(chunks), threads, 0, st>>>(a, cur, oth, lp);
+      return launched();
+    } else {
+      mp_neighbour_kernel<V><<<grid_for(words), threads, 0, st>>>(a, cur, oth, lp);
+      if ((e = launched()) != cudaSuccess) return e;
+      float* t = cur; cur = oth; oth = t;
+      return cudaSuccess;
+    }
+  };
   if constexpr (Var<V>::ot) {
     for (int b = 0; b < bp.nb; ++b)
       if ((e = fold(b, true)) != cudaSuccess) return e;
     mp_solve_kernel<V, MP_TPB><<<nsolve, MP_TPB, smem, st>>>(a, cur, K);
     if ((e = launched()) != cudaSuccess) return e;
-    // frequency phase of M4 / M8, one level per pass in gather form (a band
-    // would read its descendants bit-reversed, scattered across sectors)
-    for (int lp = MP_LOG_S + 1; lp <= logN - 2; ++lp) {
-      mp_neighbour_kernel<V><<<grid_for(words), threads, 0, st>>>(a, cur, oth, lp);
-      if ((e = launched()) != cudaSuccess) return e;
-      float* t = cur; cur = oth; oth = t;
-    }
+    for (int lp = MP_LOG_S + 1; lp <= logN - 2; ++lp)
+      if ((e = relation(lp)) != cudaSuccess) return e;
     for (int lm = MP_LOG_S + 3; lm <= logN - 1; ++lm) {
       mp_chain_kernel<V><<<grid_for(words), threads, 0, st>>>(a, cur, oth, lm);
       if ((e = launched()) != cudaSuccess) return e;
@@ -453,11 +636,8 @@ cudaError_t mp_run(const MpArgs& a0, float* W0, float* W1, const SmallConsts& K,
       if ((e = launched()) != cudaSuccess) return e;
       float* t = cur; cur = oth; oth = t;
     }
-    for (int lp = logN - 2; lp >= MP_LOG_S + 1; --lp) {
-      mp_neighbour_kernel<V><<<grid_for(words), threads, 0, st>>>(a, cur, oth, lp);
-      if ((e = launched()) != cudaSuccess) return e;
-      float* t = cur; cur = oth; oth = t;
-    }
+    for (int lp = logN - 2; lp >= MP_LOG_S + 1; --lp)
+      if ((e = relation(lp)) != cudaSuccess) return e;
     mp_solve_kernel<V, MP_TPB><<<nsolve, MP_TPB, smem, st>>>(a, cur, K);
     if ((e = launched()) != cudaSuccess) return e;
     for (int b = bp.nb - 1; b >= 0; --b)

@@ -49,16 +49,6 @@ cudaError_t scratch_address(float** out) {
   return cudaSuccess;
 }
 
-cudaError_t multipass_dispatch(int variant, const MpArgs& a, float* W0, float* W1, const SmallConsts& K,
-                               cudaStream_t st, long long* nl) {
-  switch (variant) {
-    case 2: return multipass_variant_2(a, W0, W1, K, st, nl);
-    case 4: return multipass_variant_4(a, W0, W1, K, st, nl);
-    case 6: return multipass_variant_6(a, W0, W1, K, st, nl);
-    default: return multipass_variant_8(a, W0, W1, K, st, nl);
-  }
-}
-
 }  // namespace
 }  // namespace amqft
 

@@ -51,7 +51,7 @@ def batched_reference(x, lg, off, variant, inverse):
     return out
 
 
-@pytest.mark.parametrize("v,hi", [(4, 18), (2, 17), (1, 16), (8, 16), (3, 14)])
+@pytest.mark.parametrize("v,hi", [(4, 18), (2, 17), (1, 16), (8, 16), (3, 14), (1, 17), (7, 17)])
 def test_ragged_matches_batched(v, hi):
     import torch
 

@@ -36,7 +36,7 @@ def _ref(log2n, variant, x, inverse):
 
 # (log2n, variant, batch): 20 transforms of 2^17 take two chunks (15 + 5);
 # 3 of 2^20 take two (2 + 1)
-CASES = [(17, 4, 20), (18, 8, 3), (20, 2, 3), (19, 6, 2)]
+CASES = [(17, 4, 20), (18, 8, 3), (20, 2, 3), (19, 6, 2), (17, 1, 20), (18, 3, 3)]
 
 
 @pytest.mark.parametrize("log2n,variant,batch", CASES)

@@ -22,7 +22,13 @@
  *     in [2^13, 2^14) (0 for an all-zero transform), is scaled by 2^-exp
  *     exactly and rounded once to nearest even.  Exponents are clamped to
  *     [-100, 100] (outside that range the scaling saturates).
- *   - in and out are owned by the caller; they must not overlap.
+ *   - in and out are owned by the caller.  in == out is the in-place
+ *     transform (every entry point but amqft_exec_rdft): each kernel reads a
+ *     transform's whole input before it writes any of that transform's output,
+ *     and no transform's output overlaps another's input, so the result is
+ *     bit-identical to the out-of-place call.  Any other overlap is rejected
+ *     (AMQFT_ERR_INPLACE).  The transforms up to 2^AMQFT_LOG2N_FUSED_MAX then
+ *     touch one buffer: one HBM read and one write per sample, no workspace.
  *   - stream is a cudaStream_t (NULL = legacy default stream).  Calls are
  *     asynchronous on that stream and make no host synchronisation.
  *   - Return value: AMQFT_OK (0) or a negative AMQFT_ERR_* code; the
@@ -45,14 +51,14 @@ extern "C" {
 #define AMQFT_ERR_VARIANT (-2)  /* variant not in 1..8 */
 #define AMQFT_ERR_DTYPE (-3)    /* dtype not supported by this entry point */
 #define AMQFT_ERR_ALIGN (-4)    /* pointer misaligned or NULL */
-#define AMQFT_ERR_INPLACE (-5)  /* in and out overlap */
+#define AMQFT_ERR_INPLACE (-5)  /* in and out overlap without being equal */
 #define AMQFT_ERR_CUDA (-6)     /* a CUDA call or kernel launch failed */
 #define AMQFT_ERR_DEVICE (-7)   /* device is not sm_103 or lacks resources */
 #define AMQFT_ERR_ARG (-8)      /* other invalid argument (NULL plan, batch < 0, ...) */
 #define AMQFT_ERR_NOMEM (-9)    /* host or device allocation failed */
 
 #define AMQFT_LOG2N_FUSED_MAX 16 /* largest log2n of the fused single-pass kernels */
-#define AMQFT_LOG2N_MAX 24       /* largest log2n (multi-pass above 2^16, variants 2, 4, 6, 8) */
+#define AMQFT_LOG2N_MAX 28       /* largest log2n (multi-pass above 2^16) */
 
 typedef enum { AMQFT_C64 = 0, AMQFT_CBF16 = 1, AMQFT_CF16 = 2 } amqft_dtype;
 
@@ -66,8 +72,10 @@ typedef struct amqft_plan_s *amqft_plan_t;
  * Lengths up to 2^AMQFT_LOG2N_FUSED_MAX run in one fused kernel (one HBM
  * read and write per sample).  Longer transforms (every variant; the
  * recurrences of variants 1, 3, 5, 7 become chunk passes and a scan of the
- * chunk totals) run as several passes over a workspace the plan allocates: two buffers of the transform's size per transform of a
- * chunk, at most 2 GiB, the batch processed chunk by chunk.  That workspace
+ * chunk totals) run as several passes over a workspace the plan allocates:
+ * two buffers of the transform's size per transform of a chunk, at most
+ * 2 GiB or one transform's two buffers if larger (4 GiB at 2^28), the batch
+ * processed chunk by chunk.  That workspace
  * (like the staging of amqft_exec_host) belongs to the plan, so the exec calls
  * of one plan must be ordered: one stream, or streams joined by events.  Calls
  * on different plans are independent.
@@ -106,7 +114,7 @@ int amqft_exec_rdft(amqft_plan_t plan, const float *in, void *out, void *stream)
 /* Transform the plan's batch from HOST memory to HOST memory: forward
  * (direction 0) or unnormalised inverse (direction 1) of `batch` complex64
  * transforms at in (read) and out (written), both host pointers, 8-byte
- * aligned, not overlapping; page-locked memory lets the copies overlap the
+ * aligned, equal (in place) or not overlapping; page-locked memory lets the copies overlap the
  * transforms (pageable memory works, with synchronous copies).  The batch runs
  * in chunks of `chunk` transforms (0: about 64 MiB per chunk): each chunk is
  * copied to the device, transformed by the same kernels as amqft_exec_fwd/inv
@@ -145,6 +153,30 @@ int amqft_plan_info(amqft_plan_t plan, int *cluster, int *per_cta, int *threads,
  * AMQFT_ERR_ARG for a NULL plan. */
 int64_t amqft_plan_launches(amqft_plan_t plan);
 
+/* Where the kernels take the trig constants of the tree levels of
+ * periodisation M >= 256 (Sect. 7.1; the M <= 128 constants of the register
+ * leaves are kernel arguments in both modes):
+ *   AMQFT_CONST_TABLE (default): the plan's table, rounded once from long
+ *     double; the single-pass kernels stage it per CTA in shared memory.
+ *     Variants 2, 4, 6, 8 are then bit-identical to the float32 recursion.
+ *   AMQFT_CONST_FLY: the "on the fly" evaluation the paper discusses (cheap
+ *     for the 2cos / 2sin constants of variants 1, 3, 5, 7): each kernel
+ *     computes the constants from their exact angles in float32 (cospif /
+ *     sinpif after an exact fold into [0, pi/4], then 2x or 1/(2x)), staged
+ *     per CTA in shared memory by the single-pass kernels and computed at
+ *     each use by the multi-pass levels above 2^13.  The kernels read no
+ *     table.  Results differ from table mode in the last bits of the
+ *     constants (within a few ulp), so they are held to the float32
+ *     tolerance rather than to bit identity.
+ * The mode applies to every later exec call on the plan (all entry points).
+ * Errors: AMQFT_ERR_ARG (NULL plan, unknown mode). */
+#define AMQFT_CONST_TABLE 0
+#define AMQFT_CONST_FLY 1
+int amqft_plan_set_constants(amqft_plan_t plan, int mode);
+
+/* The plan's constants mode, or AMQFT_ERR_ARG for a NULL plan. */
+int amqft_plan_get_constants(amqft_plan_t plan);
+
 /* ---------------------------------------------------------------------
  * Ragged batches: many transforms of different power-of-two lengths, each at
  * its own offset, in one call that launches a fixed sequence of kernels and
@@ -169,7 +201,8 @@ int amqft_plan_ragged(amqft_plan_t *out, int max_log2n, int variant, int dtype, 
  * d_offsets[i] of in (read) and of out (written); forward (direction 0) or
  * unnormalised inverse (direction 1).  d_offsets (int64) and d_log2n (uint8)
  * are device arrays of `count` entries; in, out and d_offsets are 8-byte
- * aligned; the transforms must not overlap each other or between in and out.
+ * aligned; the transforms must not overlap each other, and in and out are
+ * equal (in place) or do not overlap.
  * Transforms whose log2 N exceeds the plan's, and multi-pass transforms beyond
  * the max_points capacity, are skipped and counted (amqft_ragged_skipped).
  * Each transform gives exactly the result of amqft_exec_fwd/inv of a plan of
@@ -211,8 +244,8 @@ int amqft_ragged_skipped(amqft_plan_t plan, int64_t *skipped);
  * with that batch.  The plan supplies length, variant and constant table and
  * its own batch is ignored: create it with batch 0 so that it holds no
  * workspace.  in/out: device pointers to batch * 2^log2n interleaved complex
- * float32 values, owned by the caller, 8-byte aligned, not overlapping.
- * Makes no device or host allocation.  Every call looks up the scratch
+ * float32 values, owned by the caller, 8-byte aligned, equal (in place) or
+ * not overlapping.  Makes no device or host allocation.  Every call looks up the scratch
  * array's address in the current context (a host-side lookup, never cached,
  * so a reset device is safe); the first call on a device may load the
  * library's module into the context, so make it before any stream capture.

@@ -69,6 +69,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.amqft_plan_info.restype = i32
         lib.amqft_plan_launches.argtypes = [vp]
         lib.amqft_plan_launches.restype = i64
+        lib.amqft_plan_set_constants.argtypes = [vp, i32]
+        lib.amqft_plan_set_constants.restype = i32
+        lib.amqft_plan_get_constants.argtypes = [vp]
+        lib.amqft_plan_get_constants.restype = i32
         _lib = lib
         return lib
 
@@ -159,6 +163,22 @@ def amqft_plan_launches(plan: int) -> int:
     return n
 
 
+AMQFT_CONST_TABLE, AMQFT_CONST_FLY = 0, 1
+
+
+def amqft_plan_set_constants(plan: int, mode: int) -> None:
+    """Band-level trig constants from the plan's table (AMQFT_CONST_TABLE) or
+    evaluated on the fly in the kernels (AMQFT_CONST_FLY)."""
+    _check(load().amqft_plan_set_constants(plan, int(mode)), "amqft_plan_set_constants")
+
+
+def amqft_plan_get_constants(plan: int) -> int:
+    m = int(load().amqft_plan_get_constants(plan))
+    if m < 0:
+        _check(m, "amqft_plan_get_constants")
+    return m
+
+
 # --- torch convenience layer ------------------------------------------------
 
 def _stream_handle(stream) -> int:
@@ -192,6 +212,17 @@ class Plan:
     def launches(self) -> int:
         """Kernels launched by this plan's exec calls so far."""
         return amqft_plan_launches(self.handle)
+
+    @property
+    def constants(self) -> str:
+        """"table" or "fly": where the kernels take the band levels' constants."""
+        return "fly" if amqft_plan_get_constants(self.handle) == AMQFT_CONST_FLY else "table"
+
+    @constants.setter
+    def constants(self, mode: str) -> None:
+        if mode not in ("table", "fly"):
+            raise ValueError(f"constants mode {mode!r} is not 'table' or 'fly'")
+        amqft_plan_set_constants(self.handle, AMQFT_CONST_FLY if mode == "fly" else AMQFT_CONST_TABLE)
 
     def _check_tensor(self, t, name):
         import torch

@@ -11,6 +11,8 @@
 #include <string.h>
 
 #include <string>
+#include <thread>
+#include <vector>
 
 #include "amqft.h"
 #include "amqft_ragged_impl.cuh"
@@ -36,8 +38,10 @@ FusedConfig fused_config(int logN, int variant) {
     c.threads = cluster_tpb(logN, variant_ot(variant));
   }
   c.tot_off = ((c.nreg * c.RS + 31) / 32) * 32;
-  // scan scratch (threads + 32), snapshot, and one 16-bit exponent slot per transform
-  c.smem = (c.tot_off + c.threads + 32 + snap_floats(c.nreg * half) + c.per_cta) * (int)sizeof(float);
+  // scan scratch (threads + 32), snapshot, one 16-bit exponent slot per
+  // transform, and the band levels' constants
+  c.smem = (c.tot_off + c.threads + 32 + snap_floats(c.nreg * half) + c.per_cta + band_consts(logN)) *
+           (int)sizeof(float);
   return c;
 }
 
@@ -179,6 +183,40 @@ static float variant_const(int v, long long M, long long j) {
   return (float)c;
 }
 
+// The level-major table: periodisation M = 16..N holds its M/8 constants at
+// [M/8 - 2, M/4 - 2).  Long tables (N/4 - 2 = 2^26 - 2 entries at 2^28; long
+// double is a software format on some hosts) are filled by several host
+// threads, each entry by the same scalar function.
+static void fill_range(float* h, long long lo, long long hi, int variant) {
+  for (long long i = lo; i < hi; ++i) {
+    long long M = 16;
+    while (M / 4 - 2 <= i) M *= 2;
+    h[i] = variant_const(variant, M, i - (M / 8 - 2));
+  }
+}
+
+static void fill_table(float* h, long long n, int variant) {
+  unsigned nt = std::thread::hardware_concurrency();
+  if (nt < 1) nt = 1;
+  if (nt > 64) nt = 64;
+  if (n < (1LL << 16) || nt == 1) {
+    fill_range(h, 0, n, variant);
+    return;
+  }
+  std::vector<std::thread> th;
+  const long long per = (n + nt - 1) / nt;
+  for (unsigned t = 0; t < nt; ++t) {
+    const long long lo = (long long)t * per, hi = lo + per < n ? lo + per : n;
+    if (lo >= hi) break;
+    try {
+      th.emplace_back(fill_range, h, lo, hi, variant);
+    } catch (...) {
+      fill_range(h, lo, hi, variant);  // no thread: this one does the range
+    }
+  }
+  for (auto& x : th) x.join();
+}
+
 // ---------------------------------------------------------------------
 // errors
 // ---------------------------------------------------------------------
@@ -205,6 +243,7 @@ struct amqft_plan_s {
   int dtype;
   int device;
   float* d_ctab;
+  int const_mode;  // AMQFT_CONST_TABLE or AMQFT_CONST_FLY
   SmallConsts small;
   FusedConfig cfg;
   // multi-pass path: two ping-pong workspaces of chunk * 4 regions
@@ -234,13 +273,19 @@ static const long long kWorkspaceBytes = 2LL << 30;
 
 namespace amqft {
 
+// The table the kernels read; NULL makes them evaluate the band levels'
+// constants on the fly.
+static const float* kernel_ctab(amqft_plan_t p) {
+  return p->const_mode == AMQFT_CONST_FLY ? nullptr : p->d_ctab;
+}
+
 int plan_view(amqft_plan_t p, PlanView* v) {
   if (!p || !v) return fail(AMQFT_ERR_ARG, "plan is NULL");
   v->log2n = p->log2n;
   v->variant = p->variant;
   v->dtype = p->dtype;
   v->device = p->device;
-  v->ctab = p->d_ctab;
+  v->ctab = kernel_ctab(p);
   v->small = &p->small;
   return AMQFT_OK;
 }
@@ -299,6 +344,7 @@ int amqft_plan(amqft_plan_t* out, int log2n, int variant, int64_t batch, int dty
   p->dtype = dtype;
   p->device = dev;
   p->d_ctab = nullptr;
+  p->const_mode = AMQFT_CONST_TABLE;
   p->d_work = nullptr;
   p->chunk = 0;
   p->RSg = 0;
@@ -322,8 +368,7 @@ int amqft_plan(amqft_plan_t* out, int log2n, int variant, int64_t batch, int dty
   const long long nhost = ntab > (long long)(LEAF - 2) ? ntab : (long long)(LEAF - 2);
   float* h = (float*)calloc((size_t)nhost, sizeof(float));
   if (!h) { delete p; return fail(AMQFT_ERR_NOMEM, "amqft_plan: host allocation failed"); }
-  for (long long M = 16; M / 8 - 2 < nhost; M *= 2)
-    for (long long j = 0; j < M / 8 && M / 8 - 2 + j < nhost; ++j) h[M / 8 - 2 + j] = variant_const(variant, M, j);
+  fill_table(h, nhost, variant);
   for (int i = 0; i < LEAF - 2; ++i) p->small.c[i] = h[i];
   p->small.cos_pi4 = (float)cos_frac(1, 8);
   if (ntab > 0) {
@@ -371,7 +416,9 @@ static int exec_n(amqft_plan_t p, long long batch, const void* in, void* out, in
   const long long N = 1LL << p->log2n;
   const uintptr_t bytes = (uintptr_t)(N * batch * (c64 ? 8 : 4));
   const uintptr_t a0 = (uintptr_t)in, b0 = (uintptr_t)out;
-  if (a0 < b0 + bytes && b0 < a0 + bytes) return fail(AMQFT_ERR_INPLACE, "in and out overlap");
+  // in == out is the in-place transform; any other overlap is rejected
+  if (a0 != b0 && a0 < b0 + bytes && b0 < a0 + bytes)
+    return fail(AMQFT_ERR_INPLACE, "in and out overlap without being equal");
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;
   if (p->log2n > AMQFT_LOG2N_FUSED_MAX) {
@@ -383,7 +430,7 @@ static int exec_n(amqft_plan_t p, long long batch, const void* in, void* out, in
       a.exp_in = exp_in;
       a.exp_out = exp_out;
       a.dtype = p->dtype;
-      a.ctab = p->d_ctab;
+      a.ctab = kernel_ctab(p);
       a.nt = (batch - t0) < p->chunk ? (batch - t0) : p->chunk;
       a.t0 = t0;
       a.logN = p->log2n;
@@ -410,7 +457,7 @@ static int exec_n(amqft_plan_t p, long long batch, const void* in, void* out, in
     return AMQFT_OK;
   }
   if (paired_supported(p->log2n, p->variant, p->dtype, batch) && !((a0 | b0) & 15u)) {
-    e = paired_launch(p->log2n, in, out, batch, inverse, p->d_ctab, p->small, st);
+    e = paired_launch(p->log2n, in, out, batch, inverse, kernel_ctab(p), p->small, st);
     if (e != cudaSuccess) return cuda_fail(e, "paired kernel launch");
     ++p->launches;
     return AMQFT_OK;
@@ -421,7 +468,7 @@ static int exec_n(amqft_plan_t p, long long batch, const void* in, void* out, in
   a.exp_in = exp_in;
   a.exp_out = exp_out;
   a.dtype = p->dtype;
-  a.ctab = p->d_ctab;
+  a.ctab = kernel_ctab(p);
   a.batch = batch;
   a.logN = p->log2n;
   a.tpc = p->cfg.per_cta;
@@ -480,7 +527,7 @@ int amqft_exec_rdft(amqft_plan_t p, const float* in, void* out, void* stream) {
   a.in = in;
   a.out = out;
   a.dtype = AMQFT_C64;
-  a.ctab = p->d_ctab;
+  a.ctab = kernel_ctab(p);
   a.batch = (p->batch + 1) / 2;  // one complex transform per pair of real signals
   a.nreal = p->batch;
   a.logN = p->log2n;
@@ -519,7 +566,8 @@ int amqft_exec_host(amqft_plan_t p, const void* in, void* out, int direction, in
   if (((uintptr_t)in | (uintptr_t)out) & 7u) return fail(AMQFT_ERR_ALIGN, "amqft_exec_host: in/out must be 8-byte aligned");
   const long long N = 1LL << p->log2n, tbytes = N * 8;
   const uintptr_t bytes = (uintptr_t)(tbytes * p->batch), a0 = (uintptr_t)in, b0 = (uintptr_t)out;
-  if (a0 < b0 + bytes && b0 < a0 + bytes) return fail(AMQFT_ERR_INPLACE, "amqft_exec_host: in and out overlap");
+  if (a0 != b0 && a0 < b0 + bytes && b0 < a0 + bytes)
+    return fail(AMQFT_ERR_INPLACE, "amqft_exec_host: in and out overlap without being equal");
   long long C = chunk > 0 ? chunk : (64LL << 20) / tbytes;
   if (C < 1) C = 1;
   if (C > p->batch) C = p->batch;
@@ -654,7 +702,7 @@ int amqft_exec_ragged(amqft_plan_t p, int64_t count, const int64_t* d_offsets, c
   a.in = in;
   a.out = out;
   a.dtype = AMQFT_C64;
-  a.ctab = p->d_ctab;
+  a.ctab = kernel_ctab(p);
   a.inverse = direction;
   a.toff = (const long long*)d_offsets;
   RaggedArgs r;
@@ -671,7 +719,8 @@ int amqft_exec_ragged(amqft_plan_t p, int64_t count, const int64_t* d_offsets, c
   for (int c = 1; c <= 13 && c <= r.maxlog; ++c) {
     const int tpc = small_tpc(c);
     const int sm_bytes =
-        (small_tot_off(c) + SMALL_TPB + 32 + snap_floats(4 * tpc * (1 << (c - 1))) + tpc) * (int)sizeof(float);
+        (small_tot_off(c) + SMALL_TPB + 32 + snap_floats(4 * tpc * (1 << (c - 1))) + tpc + band_consts(c)) *
+        (int)sizeof(float);
     if (sm_bytes > L.small_smem) L.small_smem = sm_bytes;
   }
   for (int q = 0; q < 3; ++q) {
@@ -693,7 +742,7 @@ int amqft_exec_ragged(amqft_plan_t p, int64_t count, const int64_t* d_offsets, c
     m.in = in;
     m.out = out;
     m.dtype = AMQFT_C64;
-    m.ctab = p->d_ctab;
+    m.ctab = kernel_ctab(p);
     m.nt = capc;
     m.t0 = 0;
     m.logN = c;
@@ -736,6 +785,21 @@ int64_t amqft_plan_launches(amqft_plan_t p) {
   t_err.clear();
   if (!p) return fail(AMQFT_ERR_ARG, "plan is NULL");
   return (int64_t)p->launches.load();
+}
+
+int amqft_plan_set_constants(amqft_plan_t p, int mode) {
+  t_err.clear();
+  if (!p) return fail(AMQFT_ERR_ARG, "plan is NULL");
+  if (mode != AMQFT_CONST_TABLE && mode != AMQFT_CONST_FLY)
+    return fail(AMQFT_ERR_ARG, "amqft_plan_set_constants: mode=%d is not AMQFT_CONST_TABLE or AMQFT_CONST_FLY", mode);
+  p->const_mode = mode;
+  return AMQFT_OK;
+}
+
+int amqft_plan_get_constants(amqft_plan_t p) {
+  t_err.clear();
+  if (!p) return fail(AMQFT_ERR_ARG, "plan is NULL");
+  return p->const_mode;
 }
 
 int amqft_plan_info(amqft_plan_t p, int* cluster, int* per_cta, int* threads, int* smem_bytes) {

@@ -17,6 +17,7 @@
 //    the same words as the inputs.
 #pragma once
 
+#include "amqft_consts.cuh"
 #include "amqft_device.cuh"
 
 namespace amqft {
@@ -53,20 +54,19 @@ __host__ __device__ constexpr int desc_block(int e) {
 }
 
 // ---- ot forward: D_k time phase + M_v time phase over R levels, one item --
-template <int V, int R, int CTX>
-__device__ __forceinline__ void fold_fwd_item(const float* Rg, int p0, int L, int i, const float* __restrict__ ctab,
+template <int V, int R, int CTX, class CS>
+__device__ __forceinline__ void fold_fwd_item(const float* Rg, int p0, int L, int i, const CS& cs,
                                               float (&x)[1 << R]) {
   constexpr int n = 1 << R;
 #pragma unroll
   for (int e = 0; e < n; ++e) x[e] = Rg[sw(p0 + fold_pos<R>(e, 0, L, i))];
 #pragma unroll
   for (int l = 0; l < R; ++l) {
-    const float* __restrict__ ct = ctab + (((L >> l) >> 1) - 2);
 #pragma unroll
     for (int e = 0; e < n; ++e) {
       if ((e >> l) & 1) continue;
       const int e2 = e | (1 << l);
-      const float c = __ldg(ct + fold_pos<R>(e, l + 1, L, i));
+      const float c = cs(L >> l, fold_pos<R>(e, l + 1, L, i));
       const float u = x[e], w = x[e2];
       if (path_ctx<V, CTX>(e, l) == 0) { x[e] = u + w; x[e2] = (u - w) * c; }
       else { x[e] = u - w; x[e2] = (u + w) * c; }
@@ -74,12 +74,12 @@ __device__ __forceinline__ void fold_fwd_item(const float* Rg, int p0, int L, in
   }
 }
 
-template <int V, int R, int CTX>
-__device__ __forceinline__ void fold_fwd_pair(float* Rg, int p0, int L, int i, const float* __restrict__ ctab) {
+template <int V, int R, int CTX, class CS>
+__device__ __forceinline__ void fold_fwd_pair(float* Rg, int p0, int L, int i, const CS& cs) {
   const int W = L >> R, i2 = W - 1 - i;
   float x[1 << R], y[1 << R];
-  fold_fwd_item<V, R, CTX>(Rg, p0, L, i, ctab, x);
-  fold_fwd_item<V, R, CTX>(Rg, p0, L, i2, ctab, y);
+  fold_fwd_item<V, R, CTX>(Rg, p0, L, i, cs, x);
+  fold_fwd_item<V, R, CTX>(Rg, p0, L, i2, cs, y);
 #pragma unroll
   for (int e = 0; e < (1 << R); ++e) {
     const int blk = p0 + desc_block<V, CTX, R>(e) * W;
@@ -89,8 +89,8 @@ __device__ __forceinline__ void fold_fwd_pair(float* Rg, int p0, int L, int i, c
 }
 
 // ---- to backward: D_n frequency phase + M_v frequency phase, one item -----
-template <int V, int R, int CTX>
-__device__ __forceinline__ void fold_bwd_item(const float* Rg, int p0, int L, int i, const float* __restrict__ ctab,
+template <int V, int R, int CTX, class CS>
+__device__ __forceinline__ void fold_bwd_item(const float* Rg, int p0, int L, int i, const CS& cs,
                                               float (&x)[1 << R]) {
   constexpr int n = 1 << R;
   const int W = L >> R;
@@ -98,12 +98,11 @@ __device__ __forceinline__ void fold_bwd_item(const float* Rg, int p0, int L, in
   for (int e = 0; e < n; ++e) x[e] = Rg[sw(p0 + desc_block<V, CTX, R>(e) * W + i)];
 #pragma unroll
   for (int l = R - 1; l >= 0; --l) {
-    const float* __restrict__ ct = ctab + (((L >> l) >> 1) - 2);
 #pragma unroll
     for (int e = 0; e < n; ++e) {
       if ((e >> l) & 1) continue;
       const int e2 = e | (1 << l);
-      const float c = __ldg(ct + fold_pos<R>(e, l + 1, L, i));
+      const float c = cs(L >> l, fold_pos<R>(e, l + 1, L, i));
       const float E = x[e], O = x[e2] * c;
       if (path_ctx<V, CTX>(e, l) == 0) { x[e] = E + O; x[e2] = E - O; }
       else { x[e] = O + E; x[e2] = O - E; }
@@ -111,12 +110,12 @@ __device__ __forceinline__ void fold_bwd_item(const float* Rg, int p0, int L, in
   }
 }
 
-template <int V, int R, int CTX>
-__device__ __forceinline__ void fold_bwd_pair(float* Rg, int p0, int L, int i, const float* __restrict__ ctab) {
+template <int V, int R, int CTX, class CS>
+__device__ __forceinline__ void fold_bwd_pair(float* Rg, int p0, int L, int i, const CS& cs) {
   const int W = L >> R, i2 = W - 1 - i;
   float x[1 << R], y[1 << R];
-  fold_bwd_item<V, R, CTX>(Rg, p0, L, i, ctab, x);
-  fold_bwd_item<V, R, CTX>(Rg, p0, L, i2, ctab, y);
+  fold_bwd_item<V, R, CTX>(Rg, p0, L, i, cs, x);
+  fold_bwd_item<V, R, CTX>(Rg, p0, L, i2, cs, y);
 #pragma unroll
   for (int e = 0; e < (1 << R); ++e) {
     Rg[sw(p0 + fold_pos<R>(e, 0, L, i))] = x[e];
@@ -124,33 +123,32 @@ __device__ __forceinline__ void fold_bwd_pair(float* Rg, int p0, int L, int i, c
   }
 }
 
-template <int V, bool FWD, int R>
-__device__ __forceinline__ void fold_pair(float* Rg, int p0, int logL, int i, int ctx, const float* __restrict__ ctab) {
+template <int V, bool FWD, int R, class CS>
+__device__ __forceinline__ void fold_pair(float* Rg, int p0, int logL, int i, int ctx, const CS& cs) {
   const int L = 1 << logL;
   if constexpr (FWD) {
-    if (ctx == 0) fold_fwd_pair<V, R, 0>(Rg, p0, L, i, ctab);
-    else fold_fwd_pair<V, R, 1>(Rg, p0, L, i, ctab);
+    if (ctx == 0) fold_fwd_pair<V, R, 0>(Rg, p0, L, i, cs);
+    else fold_fwd_pair<V, R, 1>(Rg, p0, L, i, cs);
   } else {
-    if (ctx == 0) fold_bwd_pair<V, R, 0>(Rg, p0, L, i, ctab);
-    else fold_bwd_pair<V, R, 1>(Rg, p0, L, i, ctab);
+    if (ctx == 0) fold_bwd_pair<V, R, 0>(Rg, p0, L, i, cs);
+    else fold_bwd_pair<V, R, 1>(Rg, p0, L, i, cs);
   }
 }
 
 // the trees whose roots lie inside the band: root size L >> q, R - q levels
-template <int V, bool FWD, int R, int Q>
-__device__ __forceinline__ void fold_bundle(float* Rg, int half, int logL, int i, int ctx0,
-                                            const float* __restrict__ ctab) {
+template <int V, bool FWD, int R, int Q, class CS>
+__device__ __forceinline__ void fold_bundle(float* Rg, int half, int logL, int i, int ctx0, const CS& cs) {
   if constexpr (Q < R) {
-    fold_pair<V, FWD, R - Q>(Rg, half - (2 << (logL - Q)), logL - Q, i, ctx0, ctab);
-    fold_bundle<V, FWD, R, Q + 1>(Rg, half, logL, i, ctx0, ctab);
+    fold_pair<V, FWD, R - Q>(Rg, half - (2 << (logL - Q)), logL - Q, i, ctx0, cs);
+    fold_bundle<V, FWD, R, Q + 1>(Rg, half, logL, i, ctx0, cs);
   }
 }
 
 // A fold band over every region of the CTA (GRID: of the whole grid, the
 // regions then living in global memory).  Work groups: item pairs of the
 // class-0 nodes (size L, blocks [0, half - L)), then pairs of the bundle.
-template <int V, bool FWD, int R, int TPB, bool GRID = false>
-__device__ __forceinline__ void run_fold_band(float* sm, const Geo& g, int logL, const float* __restrict__ ctab) {
+template <int V, bool FWD, int R, int TPB, bool GRID = false, class CS>
+__device__ __forceinline__ void run_fold_band(float* sm, const Geo& g, int logL, const CS& cs) {
   const int logW = logL - R, W2 = 1 << (logW - 1);
   const unsigned nb0 = nodes_at(g, logL);
   const unsigned per = (nb0 + (g.sub ? 0u : 1u)) << (logW - 1);  // groups per region (+ bundle)
@@ -166,9 +164,9 @@ __device__ __forceinline__ void run_fold_band(float* sm, const Geo& g, int logL,
     const int i = (int)(gidx & (unsigned)(W2 - 1));
     if (b < nb0) {
       const int p0 = (int)(b << logL);
-      fold_pair<V, FWD, R>(Rg, p0, logL, i, node_ctx_g<V>(g, p0, logL, c0), ctab);
+      fold_pair<V, FWD, R>(Rg, p0, logL, i, node_ctx_g<V>(g, p0, logL, c0), cs);
     } else {
-      fold_bundle<V, FWD, R, 1>(Rg, g.half, logL, i, c0, ctab);
+      fold_bundle<V, FWD, R, 1>(Rg, g.half, logL, i, c0, cs);
     }
   }
 }
@@ -338,22 +336,21 @@ __device__ __forceinline__ void run_chunk_band(float* sm, float* snap, const Geo
   }
 }
 
-template <int V, int TPB>
-__device__ __forceinline__ void run_fold_band_r(float* sm, const Geo& g, int logL, int R, bool fwd,
-                                                const float* __restrict__ ctab) {
+template <int V, int TPB, class CS>
+__device__ __forceinline__ void run_fold_band_r(float* sm, const Geo& g, int logL, int R, bool fwd, const CS& cs) {
   if (fwd) {
     switch (R) {
-      case 1: run_fold_band<V, true, 1, TPB>(sm, g, logL, ctab); break;
-      case 2: run_fold_band<V, true, 2, TPB>(sm, g, logL, ctab); break;
-      case 3: run_fold_band<V, true, 3, TPB>(sm, g, logL, ctab); break;
-      default: run_fold_band<V, true, 4, TPB>(sm, g, logL, ctab); break;
+      case 1: run_fold_band<V, true, 1, TPB>(sm, g, logL, cs); break;
+      case 2: run_fold_band<V, true, 2, TPB>(sm, g, logL, cs); break;
+      case 3: run_fold_band<V, true, 3, TPB>(sm, g, logL, cs); break;
+      default: run_fold_band<V, true, 4, TPB>(sm, g, logL, cs); break;
     }
   } else {
     switch (R) {
-      case 1: run_fold_band<V, false, 1, TPB>(sm, g, logL, ctab); break;
-      case 2: run_fold_band<V, false, 2, TPB>(sm, g, logL, ctab); break;
-      case 3: run_fold_band<V, false, 3, TPB>(sm, g, logL, ctab); break;
-      default: run_fold_band<V, false, 4, TPB>(sm, g, logL, ctab); break;
+      case 1: run_fold_band<V, false, 1, TPB>(sm, g, logL, cs); break;
+      case 2: run_fold_band<V, false, 2, TPB>(sm, g, logL, cs); break;
+      case 3: run_fold_band<V, false, 3, TPB>(sm, g, logL, cs); break;
+      default: run_fold_band<V, false, 4, TPB>(sm, g, logL, cs); break;
     }
   }
 }
@@ -373,8 +370,8 @@ __device__ __forceinline__ void run_chunk_band_r(float* sm, float* snap, const G
 // path uses the same split for the levels above its subproblem size.
 struct BandPlan {
   int nb;
-  int logL[3];
-  int R[3];
+  int logL[4];  // four bands of up to RMAX levels: the 13 levels above 2^13 of N = 2^28
+  int R[4];
 };
 
 __host__ __device__ __forceinline__ BandPlan band_plan(int logN, int log_bottom = LOG_LEAF) {
@@ -382,7 +379,7 @@ __host__ __device__ __forceinline__ BandPlan band_plan(int logN, int log_bottom 
   int nl = logN - 2 - log_bottom;
   int top = logN - 2;
   b.nb = 0;
-  while (nl > 0 && b.nb < 3) {
+  while (nl > 0 && b.nb < 4) {
     const int nbands = (nl + RMAX - 1) / RMAX;
     const int R = (nl + nbands - 1) / nbands;
     b.logL[b.nb] = top;

@@ -573,6 +573,11 @@ struct Geo {
 // Transforms per CTA of the single-CTA path (N <= 2^13): 16384 region values.
 __host__ __device__ constexpr int small_tpc(int logN) { return (512 * 32) / ((1 << logN) >= 4 ? 2 * (1 << logN) : 8); }
 
+// Constants of the band levels of a transform of 2^logN (node sizes 2^6 ..
+// N/4, periodisations 256 .. N: table entries 30 .. N/4 - 3), staged per CTA
+// in shared memory after the exponent slots.
+__host__ __device__ constexpr int band_consts(int logN) { return logN >= 8 ? (1 << (logN - 2)) - 32 : 0; }
+
 // context of region (or node) r: region mode, C1 S1 C2 S2 alternate DCT/DST;
 // node mode, gbase is a bit mask of the nodes' root contexts
 __device__ __forceinline__ int ctx_of(const Geo& g, int r) {

@@ -689,7 +689,7 @@ __device__ __forceinline__ void store_natural_cluster(float* sm, const FusedArgs
 // between the load and the store.  cctx: the region context on the cluster
 // path (LN > 0), where the final chain pair writes natural order.
 template <int V, int TPB, int MAXI, int CL, int LN>
-__device__ __forceinline__ void fused_compute(float* sm, const Geo& g, const float* __restrict__ ctab,
+__device__ __forceinline__ void fused_compute(float* sm, const Geo& g, const TabConsts& ctab,
                                               const SmallConsts& K, float* tot, float* wsum, float* snap, int cctx) {
   const int logN = LN > 0 ? LN : g.logN, half = 1 << (logN - 1);
   (void)tot;
@@ -825,6 +825,11 @@ __device__ __forceinline__ void fused_body(const FusedArgs& a, const SmallConsts
   float* tot = sm + tot_off;
   float* wsum = tot + TPB;
   float* snap = wsum + 32;
+  // the band levels' constants (table entries 30 ..), after the exponent
+  // slots: copied from the plan's table, or evaluated on the fly (ctab NULL);
+  // visible to the bands after the barrier that ends the load
+  float* cst = snap + snap_floats(g.nreg_cap * half) + (CL == 1 ? small_tpc(logN) : 1);
+  stage_consts<V>(cst, band_consts(logN), a.ctab, (int)threadIdx.x, TPB);
 
   // ---- load ----
   // every configuration gives each thread exactly NIT orbit items, taken in
@@ -865,7 +870,7 @@ __device__ __forceinline__ void fused_body(const FusedArgs& a, const SmallConsts
   else cg::this_cluster().sync();
 
   // ---- trees and chain ----
-  fused_compute<V, TPB, MAXI, CL, LN>(sm, g, a.ctab, K, tot, wsum, snap,
+  fused_compute<V, TPB, MAXI, CL, LN>(sm, g, TabConsts{cst}, K, tot, wsum, snap,
                                       CL > 1 ? (int)cg::this_cluster().block_rank() & 1 : 0);
 
   // ---- store ----

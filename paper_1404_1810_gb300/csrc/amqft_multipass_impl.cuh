@@ -37,7 +37,7 @@ struct MpArgs {
   const int* exp_in;   // 16-bit input: per-transform exponents (NULL: all 0)
   int* exp_out;        // 16-bit output: per-transform exponents
   int dtype;
-  const float* ctab;
+  const float* ctab;   // the plan's constant table; NULL: constants evaluated on the fly
   long long nt;       // transforms in this chunk
   long long t0;       // first transform of the chunk (for in/out)
   int logN;
@@ -161,7 +161,8 @@ __device__ __forceinline__ Geo mp_geo(const MpArgs& a) {
 template <int V, bool FWD, int R>
 __global__ void __launch_bounds__(256) mp_fold_band_kernel(MpArgs a, float* W, int logL) {
   const Geo g = mp_geo(a);
-  run_fold_band<V, FWD, R, 256, true>(W, g, logL, a.ctab);
+  if (a.ctab) run_fold_band<V, FWD, R, 256, true>(W, g, logL, TabConsts{a.ctab + 30});
+  else run_fold_band<V, FWD, R, 256, true>(W, g, logL, FlyConsts<V>{});
 }
 
 // Neighbour form of M_v on the B halves at node size 2^logLp (M4/M8
@@ -423,6 +424,12 @@ __global__ void __launch_bounds__(TPB) mp_solve_kernel(MpArgs a, float* W, const
   float* tot = sm + 2 * RSn + 64;  // scratch after the largest layout (tail: 2S + 32 words)
   float* wsum = tot + TPB;
   float* snap = wsum + 32;
+  // constants of the node levels up to S (periodisations up to 4S), staged
+  // from the table or evaluated on the fly; visible after the barrier that
+  // ends the copy-in below
+  float* cst = snap + snap_floats(2 * MP_S);
+  stage_consts<V>(cst, band_consts(MP_LOG_S + 2), a.ctab, (int)threadIdx.x, TPB);
+  const TabConsts cs{cst};
   Geo g;
   if (sidx < nnode / 2) {
     // node mode: nodes 2*sidx and 2*sidx + 1
@@ -445,7 +452,7 @@ __global__ void __launch_bounds__(TPB) mp_solve_kernel(MpArgs a, float* W, const
     const int nleaf = MP_S >> LOG_LEAF;
     if constexpr (Var<V>::ot) {
       for (int b = 0; b < bp.nb; ++b) {
-        run_fold_band_r<V, TPB>(sm, g, bp.logL[b], bp.R[b], true, a.ctab);
+        run_fold_band_r<V, TPB>(sm, g, bp.logL[b], bp.R[b], true, cs);
         __syncthreads();
       }
       for (int w = threadIdx.x; w < 2 * nleaf; w += TPB) {
@@ -476,7 +483,7 @@ __global__ void __launch_bounds__(TPB) mp_solve_kernel(MpArgs a, float* W, const
       }
       __syncthreads();
       for (int b = bp.nb - 1; b >= 0; --b) {
-        run_fold_band_r<V, TPB>(sm, g, bp.logL[b], bp.R[b], false, a.ctab);
+        run_fold_band_r<V, TPB>(sm, g, bp.logL[b], bp.R[b], false, cs);
         __syncthreads();
       }
     }
@@ -502,7 +509,7 @@ __global__ void __launch_bounds__(TPB) mp_solve_kernel(MpArgs a, float* W, const
     const int nleaf = (halfp >> LOG_LEAF) - 1;
     if constexpr (Var<V>::ot) {
       for (int b = 0; b < bp.nb; ++b) {
-        run_fold_band_r<V, TPB>(sm, g, bp.logL[b], bp.R[b], true, a.ctab);
+        run_fold_band_r<V, TPB>(sm, g, bp.logL[b], bp.R[b], true, cs);
         __syncthreads();
       }
       for (int w = threadIdx.x; w < nleaf + 1; w += TPB) {
@@ -541,7 +548,7 @@ __global__ void __launch_bounds__(TPB) mp_solve_kernel(MpArgs a, float* W, const
         run_leaf<V>(sm, w << LOG_LEAF, node_ctx_g<V>(g, w << LOG_LEAF, LOG_LEAF, ctx0), K);
       __syncthreads();
       for (int b = bp.nb - 1; b >= 0; --b) {
-        run_fold_band_r<V, TPB>(sm, g, bp.logL[b], bp.R[b], false, a.ctab);
+        run_fold_band_r<V, TPB>(sm, g, bp.logL[b], bp.R[b], false, cs);
         __syncthreads();
       }
     }
@@ -550,8 +557,10 @@ __global__ void __launch_bounds__(TPB) mp_solve_kernel(MpArgs a, float* W, const
 }
 
 inline int mp_solve_smem_bytes() {
-  // tail layout (2S + 32 words) is the larger one; then scan scratch and snapshot
-  return (2 * (MP_S + 32) + 64 + MP_TPB + 32 + snap_floats(2 * MP_S)) * (int)sizeof(float);
+  // tail layout (2S + 32 words) is the larger one; then scan scratch,
+  // snapshot and the node levels' constants
+  return (2 * (MP_S + 32) + 64 + MP_TPB + 32 + snap_floats(2 * MP_S) + band_consts(MP_LOG_S + 2)) *
+         (int)sizeof(float);
 }
 
 // Host side: the whole sequence for one chunk of transforms.

@@ -75,7 +75,8 @@ extern "C" int amqft_exec_static(amqft_plan_t plan, int64_t batch, const void* i
   const long long N = 1LL << pv.log2n;
   const uintptr_t bytes = (uintptr_t)(N * batch * 8);
   const uintptr_t a0 = (uintptr_t)in, b0 = (uintptr_t)out;
-  if (a0 < b0 + bytes && b0 < a0 + bytes) return set_error(AMQFT_ERR_INPLACE, "amqft_exec_static: in and out overlap");
+  if (a0 != b0 && a0 < b0 + bytes && b0 < a0 + bytes)
+    return set_error(AMQFT_ERR_INPLACE, "amqft_exec_static: in and out overlap without being equal");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return set_error(AMQFT_ERR_CUDA, "amqft_exec_static: cudaGetDevice: %s", cudaGetErrorString(e));

@@ -894,7 +894,8 @@ PR_HD void paired_body(Ctx& cx, const float2* __restrict__ in, float2* __restric
   constexpr long long N = 1LL << LN;
   const int r = cx.rank, tid = cx.tid;
   const int ncst = (r & 1) == 0 ? (1 << T) - 32 : (1 << (T - 1)) - 32;
-  for (int i = tid; i < ncst; i += NT) cst[i] = ctab[30 + i];
+  if (ctab)  // else the kernel has evaluated them on the fly
+    for (int i = tid; i < ncst; i += NT) cst[i] = ctab[30 + i];
   LoadRound<LN> R;
   if (cid < batch) load_fetch<LN>(cx, in + (long long)cid * N, r, 0, R);
   for (int t = cid; t < batch; t += ncl) {

@@ -3,6 +3,7 @@
 // Instantiated per transform length in amqft_paired_l{14,15,16}.cu.
 #pragma once
 #include "amqft_internal.h"
+#include "amqft_consts.cuh"
 #include "amqft_device.cuh"
 #include "amqft_paired.cuh"
 
@@ -77,6 +78,10 @@ __global__ void __launch_bounds__(paired_tpb(LN), paired_ctas(LN))
   cx.rank = (int)cl.block_rank();
   cx.lbase = (unsigned)__cvta_generic_to_shared(psm);
   float* cst = reinterpret_cast<float*>(psm + region_f2<T>());
+  if (!ctab) {  // constants on the fly: the same entries paired_body copies from the table
+    const int ncst = (cx.rank & 1) == 0 ? (1 << T) - 32 : (1 << (T - 1)) - 32;
+    for (int i = cx.tid; i < ncst; i += paired_tpb(LN)) cst[i] = fly_entry<4>(30 + i);
+  }
   paired_body<LN, INV>(cx, in, out, (int)batch, (int)(blockIdx.x >> 2), (int)(gridDim.x >> 2), psm, cst,
                        ctab, K);
 }

@@ -56,6 +56,10 @@ def test_argument_checks_need_no_gpu(lib):
     lib.amqft_plan_launches.argtypes = [ctypes.c_void_p]
     lib.amqft_plan_launches.restype = ctypes.c_int64
     assert lib.amqft_plan_launches(None) == -8
+    lib.amqft_plan_set_constants.argtypes = [ctypes.c_void_p, ctypes.c_int]
+    assert lib.amqft_plan_set_constants(None, 1) == -8
+    lib.amqft_plan_get_constants.argtypes = [ctypes.c_void_p]
+    assert lib.amqft_plan_get_constants(None) == -8
 
 
 def test_binding_fails_loudly_without_library(tmp_path):

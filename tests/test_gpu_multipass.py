@@ -118,6 +118,65 @@ def test_multipass_2pow24_properties(v):
     assert rel(z, n * x[0]) < 1e-3
 
 
+def dft_bins_device(x, ks):
+    """The DFT definition (Eq. qft_0A) at a few bins in float64 on the device:
+    the angle index n*k is reduced modulo N in exact integer arithmetic."""
+    import math
+
+    import torch
+
+    n = x.numel()
+    idx = torch.arange(n, dtype=torch.int64, device=x.device)
+    xd = x.to(torch.complex128)
+    out = []
+    for k in ks:
+        ang = ((idx * int(k)) % n).to(torch.float64) * (-2.0 * math.pi / n)
+        out.append(complex(torch.sum(xd * torch.polar(torch.ones_like(ang), ang)).item()))
+        del ang
+    return np.array(out)
+
+
+@pytest.fixture(scope="module")
+def e32_2pow20(orc):
+    """rel-L2 of the paper's recursion in float32 at 2^20 (variant 4), the
+    anchor of the large-N tolerance."""
+    x = synth.normal_complex(1 << 20, 1, config=2, stream=580)[0].astype(np.complex64).astype(np.complex128)
+    return rel(orc.amqft(x, 4, prec="f32"), orc.amqft(x, 4))
+
+
+@pytest.mark.parametrize("log2n,v", [(25, 4), (25, 1), (26, 2)])
+def test_multipass_very_large(e32_2pow20, log2n, v):
+    """2^25..2^28, one transform: sampled bins against the definition,
+    Parseval and the inverse.  The float32 recursion's error grows like
+    sqrt(N) (measured 2^16..2^24), so the bound is 4x the 2^20 anchor scaled
+    by sqrt(N / 2^20)."""
+    import torch
+
+    from paper_1404_1810_gb300 import Plan
+
+    n = 1 << log2n
+    x = synth.device_normal_complex64(n, 1, "cuda", seed_offset=log2n)
+    p = Plan(log2n, v, 1)
+    try:
+        y = p.fwd(x)
+        z = p.inv(y)
+        torch.cuda.synchronize()
+    finally:
+        p.close()
+    tol = 4.0 * e32_2pow20 * np.sqrt(n / (1 << 20))
+    assert bool(torch.isfinite(y).all())
+    gen = np.random.default_rng(log2n)
+    ks = [0, 1, n // 4, n // 2, n - 1] + [int(k) for k in gen.integers(0, n, 11)]
+    ref = dft_bins_device(x[0], ks)
+    got = y[0, ks].cpu().numpy().astype(np.complex128)
+    assert rel(got, ref) <= tol, (rel(got, ref), tol)
+    e_in = torch.sum(torch.abs(x[0].to(torch.complex128)) ** 2).item()
+    e_out = torch.sum(torch.abs(y[0].to(torch.complex128)) ** 2).item()
+    assert abs(e_out / (n * e_in) - 1.0) <= tol
+    d = torch.linalg.vector_norm((z[0] - n * x[0]).to(torch.complex128)).item()
+    assert d / (n * np.sqrt(e_in)) <= 2.0 * tol
+
+
 def test_multipass_chunked_batch(orc):
     """2^24 with a batch larger than one workspace chunk (8 transforms)."""
     n, b = 1 << 24, 9

@@ -172,7 +172,7 @@ def test_empty_batch_and_errors():
         amqft_plan(10, 9, 1)
     assert e.value.code == -2
     with pytest.raises(AmqftError) as e:
-        amqft_plan(25, 4, 1)
+        amqft_plan(29, 4, 1)
     assert e.value.code == -1
     for v in (1, 3, 5, 7):                        # recurrence variants run multi-pass too
         Plan(17, v, 1).close()

@@ -59,6 +59,9 @@ def parse_args():
                          "all variants; c3: 16-bit storage; c4: ragged batch in one CUDA graph; c5: autograd "
                          "forward+backward")
     ap.add_argument("--dtype16", default="bf16", choices=["bf16", "fp16"])
+    ap.add_argument("--constants", default="table", choices=["table", "fly", "auto"],
+                    help="band-level trig constants: the plan's table, evaluated on the fly in the kernels, or "
+                         "whichever the autotuner times faster on this workload")
     return ap.parse_args()
 
 
@@ -636,6 +639,12 @@ def main():
     y = torch.empty_like(x)
     z = torch.empty_like(x)
     plan = Plan(args.log2n, args.variant, args.batch)
+    from paper_1404_1810_gb300.autotune import tune_constants
+    if args.constants == "auto":
+        const_tune = tune_constants(plan, x, reps=3, use_cache=False)
+    else:
+        plan.constants = args.constants
+        const_tune = None
     stream = torch.cuda.current_stream()
 
     def barrier():
@@ -743,6 +752,14 @@ def main():
                if copies.get("bound_gpts") else None}
         del xh, yh
 
+    # both constants modes' forward kernel time on this workload, after the timed region
+    mode_used = plan.constants
+    if const_tune is None:
+        const_tune = tune_constants(plan, x, reps=3, use_cache=False)
+        plan.constants = mode_used
+    constants = {"mode": mode_used, "chosen_by": "autotuner" if args.constants == "auto" else "flag",
+                 "table_kernel_ms": const_tune["table_ms"], "fly_kernel_ms": const_tune["fly_ms"]}
+
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(x[:256].cpu().numpy().astype(np.complex128), args.variant)
 
@@ -761,6 +778,7 @@ def main():
                          "algorithmic_bytes_per_launch": BYTES_PER_POINT * args.batch * n},
             "clocks": clocks,
             "e2e": e2e,
+            "constants": constants,
             "gpu_launches": launches,
             "accuracy": accuracy,
             "cpu_baseline": cpu,

@@ -1,4 +1,4 @@
-"""Autotuner for ragged plans.
+"""Autotuners: the ragged launch knobs, and the constants mode of a plan.
 
 Every combination of the ragged launch knobs (schedule of the persistent
 small-length launch, order of its work items, its CTAs per SM, and the
@@ -85,3 +85,43 @@ def tune_ragged(plan, x, log2n, offsets, out=None, reps: int = 5, use_cache: boo
                           "all": [{"knobs": k, "ms": t} for t, k in results]}
             _save_cache(cache_path, cache)
     return dict(best)
+
+
+def tune_constants(plan, x, reps: int = 5, use_cache: bool = True, cache_path: str = CACHE) -> dict:
+    """Time `plan`'s forward transform of x with the band constants read from
+    the table and evaluated on the fly (Sect. 7.1; CUDA events, median of
+    `reps` runs after a warm-up run), apply the faster mode and return
+    {"mode": ..., "table_ms": ..., "fly_ms": ...}.  Cached per device, length,
+    variant, batch and storage type."""
+    import torch
+
+    key = f"{torch.cuda.get_device_name()}|const|v{plan.variant}|n{plan.log2n}|b{plan.batch}|d{plan.dtype}"
+    with _lock:
+        cache = _load_cache(cache_path) if use_cache else {}
+        hit = cache.get(key)
+    if hit:
+        plan.constants = hit["mode"]
+        return dict(hit)
+    stream = torch.cuda.current_stream()
+    out = torch.empty_like(x)
+    res = {}
+    for mode in ("table", "fly"):
+        plan.constants = mode
+        plan.fwd(x, out)
+        times = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            plan.fwd(x, out)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+        res[mode + "_ms"] = statistics.median(times)
+    res["mode"] = "fly" if res["fly_ms"] < res["table_ms"] else "table"
+    plan.constants = res["mode"]
+    if use_cache:
+        with _lock:
+            cache = _load_cache(cache_path)
+            cache[key] = res
+            _save_cache(cache_path, cache)
+    return dict(res)

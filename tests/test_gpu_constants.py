@@ -148,3 +148,25 @@ def test_mode_errors():
             p.constants = "disk"
     finally:
         p.close()
+
+
+def test_constants_autotuner(tmp_path):
+    import torch
+
+    from paper_1404_1810_gb300 import Plan
+    from paper_1404_1810_gb300.autotune import tune_constants
+
+    x = synth.device_normal_complex64(1 << 12, 64, "cuda")
+    p = Plan(12, 1, 64)
+    try:
+        cache = str(tmp_path / "tune.json")
+        r = tune_constants(p, x, reps=2, cache_path=cache)
+        assert r["mode"] in ("table", "fly") and p.constants == r["mode"]
+        assert r["table_ms"] > 0 and r["fly_ms"] > 0
+        assert r["mode"] == ("fly" if r["fly_ms"] < r["table_ms"] else "table")
+        p.constants = "table" if r["mode"] == "fly" else "fly"
+        again = tune_constants(p, x, reps=2, cache_path=cache)     # served from the cache
+        assert again["mode"] == r["mode"] and p.constants == r["mode"]
+        torch.cuda.synchronize()
+    finally:
+        p.close()

@@ -144,12 +144,14 @@ def e32_2pow20(orc):
     return rel(orc.amqft(x, 4, prec="f32"), orc.amqft(x, 4))
 
 
-@pytest.mark.parametrize("log2n,v", [(25, 4), (25, 1), (26, 2)])
+@pytest.mark.parametrize("log2n,v", [(25, 4), (25, 1), (26, 2), (27, 1), (28, 4)])
 def test_multipass_very_large(e32_2pow20, log2n, v):
     """2^25..2^28, one transform: sampled bins against the definition,
     Parseval and the inverse.  The float32 recursion's error grows like
-    sqrt(N) (measured 2^16..2^24), so the bound is 4x the 2^20 anchor scaled
-    by sqrt(N / 2^20)."""
+    sqrt(N) (measured 2^12..2^24), so the bound is 4x the 2^20 anchor scaled
+    by sqrt(N / 2^20).  (Variant 3 is left out here: its float32 recursion
+    concentrates a much larger error on the lowest harmonics and those next
+    to N/2, test_variant3_low_harmonics.)"""
     import torch
 
     from paper_1404_1810_gb300 import Plan
@@ -175,6 +177,23 @@ def test_multipass_very_large(e32_2pow20, log2n, v):
     assert abs(e_out / (n * e_in) - 1.0) <= tol
     d = torch.linalg.vector_norm((z[0] - n * x[0]).to(torch.complex128)).item()
     assert d / (n * np.sqrt(e_in)) <= 2.0 * tol
+
+
+def test_variant3_low_harmonics(orc):
+    """Variant 3's float32 recursion loses accuracy on the harmonics next to
+    0 and N/2 (the M3 time-phase recurrence; at 2^20 their error is ~100x the
+    typical bin's, growing about like N^(2/3)).  The multi-pass path, whose
+    recurrences run as chunk scans, must show the same behaviour and no
+    more: its error on those bins within 8x of the float32 recursion's."""
+    n = 1 << 20
+    x = synth.normal_complex(n, 1, config=2, stream=590)[0].astype(np.complex64).astype(np.complex128)
+    y = run_gpu(x[None, :], 3)[0]
+    r32, r64 = orc.amqft(x, 3, prec="f32"), orc.amqft(x, 3)
+    ks = [1, 2, 3, n // 2 - 2, n // 2 - 1, n // 2 + 1, n // 2 + 2, n - 1]
+    eg, eo = rel(y[ks], r64[ks]), rel(r32[ks], r64[ks])
+    ek = rel(np.delete(r32, ks), np.delete(r64, ks))
+    assert eo > 20 * ek            # the recursion's own low-harmonic error
+    assert eo / 8 <= eg <= 8 * eo, (eg, eo)
 
 
 def test_multipass_chunked_batch(orc):

@@ -23,7 +23,8 @@
  *     exactly and rounded once to nearest even.  Exponents are clamped to
  *     [-100, 100] (outside that range the scaling saturates).
  *   - in and out are owned by the caller.  in == out is the in-place
- *     transform (every entry point but amqft_exec_rdft): each kernel reads a
+ *     transform (every entry point but amqft_exec_rdft / amqft_exec_irdft;
+ *     amqft_exec_dct_dst per kind): each kernel reads a
  *     transform's whole input before it writes any of that transform's output,
  *     and no transform's output overlaps another's input, so the result is
  *     bit-identical to the out-of-place call.  Any other overlap is rejected
@@ -106,10 +107,39 @@ int amqft_exec_inv(amqft_plan_t plan, const void *in, const int32_t *exp_in, voi
  * its regions C1, S1 and C2, S2 (Sect. 3.1-3.2) are the DCT-0 / DST-0 of a and
  * of b, and R = DCT - i DST (Eq. qft_24-25), so the input costs 4 bytes a
  * point.  Each harmonic equals the complex transform of the signal with a zero
- * imaginary part.  N <= 2^AMQFT_LOG2N_FUSED_MAX; in 4-byte, out 8-byte aligned,
- * not overlapping.  Errors: AMQFT_ERR_ARG, AMQFT_ERR_N, AMQFT_ERR_DTYPE (16-bit
- * plans), AMQFT_ERR_ALIGN, AMQFT_ERR_INPLACE, AMQFT_ERR_CUDA. */
+ * imaginary part.  Every length of the plan (the multi-pass path above
+ * 2^AMQFT_LOG2N_FUSED_MAX); in 4-byte, out 8-byte aligned, not overlapping.
+ * Errors: AMQFT_ERR_ARG, AMQFT_ERR_DTYPE (16-bit plans), AMQFT_ERR_ALIGN,
+ * AMQFT_ERR_INPLACE, AMQFT_ERR_CUDA. */
 int amqft_exec_rdft(amqft_plan_t plan, const float *in, void *out, void *stream);
+
+/* Inverse of amqft_exec_rdft, unnormalised: `batch` half spectra at in
+ * (N/2 + 1 complex64 values each, harmonics 0 .. N/2 of a real signal; the
+ * imaginary parts of harmonics 0 and N/2 are taken as given) to the real
+ * signals N * x at out (N float32 each).  Two spectra share one complex
+ * transform: Z = X_a + i X_b with the Hermitian extension X(N - k) =
+ * conj X(k), and out = conj(DFT(conj Z)) splits into N x_a (real part) and
+ * N x_b (imaginary part).  log2n >= 1; in 8-byte, out 4-byte aligned, not
+ * overlapping.  Errors: AMQFT_ERR_ARG, AMQFT_ERR_N, AMQFT_ERR_DTYPE,
+ * AMQFT_ERR_ALIGN, AMQFT_ERR_INPLACE, AMQFT_ERR_CUDA. */
+int amqft_exec_irdft(amqft_plan_t plan, const void *in, float *out, void *stream);
+
+/* DCT-0 and DST-0 of periodisation N = 2^log2n (Eq. qft_0B-0C, theta =
+ * 2 pi / N): S(k) = sum_{n=0}^{N/2} s(n) cos(theta n k), k = 0..N/2, and
+ * S(k) = sum_{n=1}^{N/2-1} s(n) sin(theta n k), k = 1..N/2-1; the recursion's
+ * dct(N) and dst(N) (Sect. 4-6) without D_c / D_r around them.  count
+ * (<= the plan's batch) signals of each kind: DCT-0 inputs at dct_in, N/2 + 1
+ * floats each (n = 0..N/2), results at dct_out alike; DST-0 inputs at
+ * dst_in, N/2 - 1 floats each (n = 1..N/2-1 at [n - 1]), results at dst_out
+ * alike (k at [k - 1]).  Either pair may be NULL (that kind is not
+ * computed); a DCT-0 pair and a DST-0 pair of two signals each share one
+ * complex transform's four regions.  Each kind may run in place (dct_in ==
+ * dct_out, dst_in == dst_out); no other overlap.  log2n >= 2; arrays 4-byte
+ * aligned.  Errors: AMQFT_ERR_ARG (count outside [0, batch]), AMQFT_ERR_N,
+ * AMQFT_ERR_DTYPE, AMQFT_ERR_ALIGN (misaligned, or only one pointer of a
+ * pair), AMQFT_ERR_INPLACE, AMQFT_ERR_CUDA. */
+int amqft_exec_dct_dst(amqft_plan_t plan, int64_t count, const float *dct_in, float *dct_out,
+                       const float *dst_in, float *dst_out, void *stream);
 
 /* Transform the plan's batch from HOST memory to HOST memory: forward
  * (direction 0) or unnormalised inverse (direction 1) of `batch` complex64

@@ -61,6 +61,10 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.amqft_ragged_skipped.restype = i32
         lib.amqft_exec_rdft.argtypes = [vp, vp, vp, vp]
         lib.amqft_exec_rdft.restype = i32
+        lib.amqft_exec_irdft.argtypes = [vp, vp, vp, vp]
+        lib.amqft_exec_irdft.restype = i32
+        lib.amqft_exec_dct_dst.argtypes = [vp, i64, vp, vp, vp, vp, vp]
+        lib.amqft_exec_dct_dst.restype = i32
         lib.amqft_exec_host.argtypes = [vp, vp, vp, i32, i64, vp]
         lib.amqft_exec_host.restype = i32
         lib.amqft_exec_static.argtypes = [vp, i64, vp, vp, i32, vp]
@@ -108,6 +112,16 @@ def amqft_exec_static(plan: int, batch: int, d_in: int, d_out: int, inverse: int
 
 def amqft_exec_rdft(plan: int, d_in: int, d_out: int, stream: int = 0) -> None:
     _check(load().amqft_exec_rdft(plan, d_in, d_out, stream or None), "amqft_exec_rdft")
+
+
+def amqft_exec_irdft(plan: int, d_in: int, d_out: int, stream: int = 0) -> None:
+    _check(load().amqft_exec_irdft(plan, d_in, d_out, stream or None), "amqft_exec_irdft")
+
+
+def amqft_exec_dct_dst(plan: int, count: int, dct_in: int, dct_out: int, dst_in: int, dst_out: int,
+                       stream: int = 0) -> None:
+    _check(load().amqft_exec_dct_dst(plan, int(count), dct_in or None, dct_out or None, dst_in or None,
+                                     dst_out or None, stream or None), "amqft_exec_dct_dst")
 
 
 def amqft_exec_host(plan: int, h_in: int, h_out: int, direction: int = 0, chunk: int = 0, stream: int = 0) -> None:
@@ -296,6 +310,51 @@ class Plan:
             raise ValueError("out must be a contiguous complex64 tensor of batch x (N/2 + 1)")
         amqft_exec_rdft(self.handle, x.data_ptr(), out.data_ptr(), _stream_handle(stream))
         return out
+
+    def irdft(self, x, out=None, stream=None):
+        """Unnormalised inverse of rdft: (batch, N/2 + 1) complex64 half spectra ->
+        (batch, N) float32 signals N * x."""
+        import torch
+
+        if self.dtype != AMQFT_C64:
+            raise ValueError("irdft needs a complex64 plan")
+        h = self.n // 2 + 1
+        if x.dtype != torch.complex64 or not x.is_cuda or not x.is_contiguous() or x.numel() != self.batch * h:
+            raise ValueError(f"x must be a contiguous complex64 CUDA tensor of {self.batch} x {h}")
+        if out is None:
+            out = torch.empty((self.batch, self.n), dtype=torch.float32, device=x.device)
+        if out.dtype != torch.float32 or not out.is_contiguous() or out.numel() != self.batch * self.n:
+            raise ValueError("out must be a contiguous float32 tensor of batch x N")
+        amqft_exec_irdft(self.handle, x.data_ptr(), out.data_ptr(), _stream_handle(stream))
+        return out
+
+    def dct_dst(self, dct=None, dst=None, dct_out=None, dst_out=None, stream=None):
+        """DCT-0 (Eq. qft_0B) of the rows of `dct` (count x (N/2 + 1) float32) and
+        DST-0 (Eq. qft_0C) of the rows of `dst` (count x (N/2 - 1), sample n at
+        column n - 1), either may be None; returns (dct_out, dst_out)."""
+        import torch
+
+        if self.dtype != AMQFT_C64:
+            raise ValueError("dct_dst needs a complex64 plan")
+        count = None
+        for t, w, name in ((dct, self.n // 2 + 1, "dct"), (dst, self.n // 2 - 1, "dst")):
+            if t is None:
+                continue
+            if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or t.dim() != 2 or t.shape[1] != w:
+                raise ValueError(f"{name} must be a contiguous float32 CUDA tensor of count x {w}")
+            if count is not None and t.shape[0] != count:
+                raise ValueError("dct and dst differ in count")
+            count = t.shape[0]
+        if count is None:
+            return None, None
+        if dct is not None and dct_out is None:
+            dct_out = torch.empty_like(dct)
+        if dst is not None and dst_out is None:
+            dst_out = torch.empty_like(dst)
+        ptr = lambda t: t.data_ptr() if t is not None else 0  # noqa: E731
+        amqft_exec_dct_dst(self.handle, count, ptr(dct), ptr(dct_out), ptr(dst), ptr(dst_out),
+                           _stream_handle(stream))
+        return dct_out, dst_out
 
     def _host(self, x, out, inverse, chunk, stream):
         import torch

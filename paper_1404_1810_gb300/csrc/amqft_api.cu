@@ -424,7 +424,7 @@ static int exec_n(amqft_plan_t p, long long batch, const void* in, void* out, in
   if (p->log2n > AMQFT_LOG2N_FUSED_MAX) {
     const long long per_buf = p->chunk * 4 * p->RSg;
     for (long long t0 = 0; t0 < batch; t0 += p->chunk) {
-      MpArgs a;
+      MpArgs a = {};
       a.in = in;
       a.out = out;
       a.exp_in = exp_in;
@@ -463,6 +463,7 @@ static int exec_n(amqft_plan_t p, long long batch, const void* in, void* out, in
     return AMQFT_OK;
   }
   FusedArgs a;
+  memset(&a, 0, sizeof a);
   a.in = in;
   a.out = out;
   a.exp_in = exp_in;
@@ -497,14 +498,74 @@ int amqft_exec_inv(amqft_plan_t p, const void* in, const int32_t* exp_in, void* 
   return exec_n(p, p->batch, in, out, 1, exp_in, exp_out, stream);
 }
 
+// Special input / output forms (real input, DCT-0 / DST-0, inverse real):
+// nsig signals, two per complex transform of the plan's length, on the fused
+// kernels up to 2^16 and the multi-pass path above.
+enum { SP_RDFT, SP_TRIG, SP_IRDFT };
+
+static int exec_special(amqft_plan_t p, int mode, long long nsig, const void* in, void* out, const float* in2,
+                        float* out2, void* stream, const char* who) {
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  const long long slots = (nsig + 1) / 2;
+  const int inverse = mode == SP_IRDFT ? 1 : 0;
+  if (p->log2n > AMQFT_LOG2N_FUSED_MAX) {
+    const long long per_buf = p->chunk * 4 * p->RSg;
+    for (long long t0 = 0; t0 < slots; t0 += p->chunk) {
+      MpArgs a = {};
+      a.in = in;
+      a.out = out;
+      a.in2 = in2;
+      a.out2 = out2;
+      a.dtype = AMQFT_C64;
+      a.ctab = kernel_ctab(p);
+      a.nt = (slots - t0) < p->chunk ? (slots - t0) : p->chunk;
+      a.t0 = t0;
+      a.logN = p->log2n;
+      a.inverse = inverse;
+      a.RSg = p->RSg;
+      a.nreal = mode == SP_RDFT ? nsig : 0;
+      a.ntrig = mode == SP_TRIG ? nsig : 0;
+      a.nirdft = mode == SP_IRDFT ? nsig : 0;
+      long long nl = 0;
+      e = multipass_dispatch(p->variant, a, p->d_work, p->d_work + per_buf, p->small, st, &nl);
+      p->launches += nl;
+      if (e != cudaSuccess) return cuda_fail(e, who);
+    }
+    return AMQFT_OK;
+  }
+  FusedArgs a;
+  memset(&a, 0, sizeof a);
+  a.in = in;
+  a.out = out;
+  a.in2 = in2;
+  a.out2 = out2;
+  a.dtype = AMQFT_C64;
+  a.ctab = kernel_ctab(p);
+  a.batch = slots;
+  a.nreal = mode == SP_RDFT ? nsig : 0;
+  a.ntrig = mode == SP_TRIG ? nsig : 0;
+  a.nirdft = mode == SP_IRDFT ? nsig : 0;
+  a.inverse = inverse;
+  a.logN = p->log2n;
+  a.tpc = p->cfg.per_cta;
+  a.RS = p->cfg.RS;
+  a.tot_off = p->cfg.tot_off;
+  e = fused_launch(p->variant, a, p->small, p->cfg, st);
+  if (e != cudaSuccess) return cuda_fail(e, who);
+  ++p->launches;
+  return AMQFT_OK;
+}
+
+static bool ranges_overlap(uintptr_t a, uintptr_t na, uintptr_t b, uintptr_t nb) {
+  return a && b && na && nb && a < b + nb && b < a + na;
+}
+
 int amqft_exec_rdft(amqft_plan_t p, const float* in, void* out, void* stream) {
   t_err.clear();
   if (!p) return fail(AMQFT_ERR_ARG, "plan is NULL");
   if (p->ragged) return fail(AMQFT_ERR_ARG, "amqft_exec_rdft: not for ragged plans");
   if (p->dtype != AMQFT_C64) return fail(AMQFT_ERR_DTYPE, "amqft_exec_rdft: AMQFT_C64 plans only");
-  if (p->log2n > AMQFT_LOG2N_FUSED_MAX)
-    return fail(AMQFT_ERR_N, "amqft_exec_rdft: log2n=%d above %d (real input runs on the fused kernels)", p->log2n,
-                AMQFT_LOG2N_FUSED_MAX);
   if (p->batch == 0) return AMQFT_OK;
   if (!in || !out) return fail(AMQFT_ERR_ALIGN, "amqft_exec_rdft: in or out is NULL");
   if (((uintptr_t)in & 3u) || ((uintptr_t)out & 7u))
@@ -513,31 +574,58 @@ int amqft_exec_rdft(amqft_plan_t p, const float* in, void* out, void* stream) {
   const uintptr_t a0 = (uintptr_t)in, b0 = (uintptr_t)out;
   const uintptr_t ia = (uintptr_t)(N * p->batch * 4), ob = (uintptr_t)((N / 2 + 1) * p->batch * 8);
   if (a0 < b0 + ob && b0 < a0 + ia) return fail(AMQFT_ERR_INPLACE, "amqft_exec_rdft: in and out overlap");
-  cudaStream_t st = (cudaStream_t)stream;
-  cudaError_t e;
   if (p->log2n == 0) {
-    copy1_real_kernel<<<(unsigned)((p->batch + 255) / 256), 256, 0, st>>>(in, (float2*)out, p->batch);
-    e = cudaGetLastError();
+    copy1_real_kernel<<<(unsigned)((p->batch + 255) / 256), 256, 0, (cudaStream_t)stream>>>(in, (float2*)out,
+                                                                                             p->batch);
+    const cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return cuda_fail(e, "copy kernel launch");
     ++p->launches;
     return AMQFT_OK;
   }
-  FusedArgs a;
-  memset(&a, 0, sizeof a);
-  a.in = in;
-  a.out = out;
-  a.dtype = AMQFT_C64;
-  a.ctab = kernel_ctab(p);
-  a.batch = (p->batch + 1) / 2;  // one complex transform per pair of real signals
-  a.nreal = p->batch;
-  a.logN = p->log2n;
-  a.tpc = p->cfg.per_cta;
-  a.RS = p->cfg.RS;
-  a.tot_off = p->cfg.tot_off;
-  e = fused_launch(p->variant, a, p->small, p->cfg, st);
-  if (e != cudaSuccess) return cuda_fail(e, "fused kernel launch");
-  ++p->launches;
-  return AMQFT_OK;
+  return exec_special(p, SP_RDFT, p->batch, in, out, nullptr, nullptr, stream, "amqft_exec_rdft: launch");
+}
+
+int amqft_exec_irdft(amqft_plan_t p, const void* in, float* out, void* stream) {
+  t_err.clear();
+  if (!p) return fail(AMQFT_ERR_ARG, "plan is NULL");
+  if (p->ragged) return fail(AMQFT_ERR_ARG, "amqft_exec_irdft: not for ragged plans");
+  if (p->dtype != AMQFT_C64) return fail(AMQFT_ERR_DTYPE, "amqft_exec_irdft: AMQFT_C64 plans only");
+  if (p->log2n < 1) return fail(AMQFT_ERR_N, "amqft_exec_irdft: log2n=%d below 1", p->log2n);
+  if (p->batch == 0) return AMQFT_OK;
+  if (!in || !out) return fail(AMQFT_ERR_ALIGN, "amqft_exec_irdft: in or out is NULL");
+  if (((uintptr_t)in & 7u) || ((uintptr_t)out & 3u))
+    return fail(AMQFT_ERR_ALIGN, "amqft_exec_irdft: in must be 8-byte and out 4-byte aligned");
+  const long long N = 1LL << p->log2n;
+  if (ranges_overlap((uintptr_t)in, (uintptr_t)((N / 2 + 1) * p->batch * 8), (uintptr_t)out,
+                     (uintptr_t)(N * p->batch * 4)))
+    return fail(AMQFT_ERR_INPLACE, "amqft_exec_irdft: in and out overlap");
+  return exec_special(p, SP_IRDFT, p->batch, in, out, nullptr, nullptr, stream, "amqft_exec_irdft: launch");
+}
+
+int amqft_exec_dct_dst(amqft_plan_t p, int64_t count, const float* dct_in, float* dct_out, const float* dst_in,
+                       float* dst_out, void* stream) {
+  t_err.clear();
+  if (!p) return fail(AMQFT_ERR_ARG, "plan is NULL");
+  if (p->ragged) return fail(AMQFT_ERR_ARG, "amqft_exec_dct_dst: not for ragged plans");
+  if (p->dtype != AMQFT_C64) return fail(AMQFT_ERR_DTYPE, "amqft_exec_dct_dst: AMQFT_C64 plans only");
+  if (p->log2n < 2) return fail(AMQFT_ERR_N, "amqft_exec_dct_dst: log2n=%d below 2", p->log2n);
+  if (count < 0 || count > p->batch)
+    return fail(AMQFT_ERR_ARG, "amqft_exec_dct_dst: count=%lld outside [0, %lld]", (long long)count,
+                (long long)p->batch);
+  if (!dct_in != !dct_out || !dst_in != !dst_out)
+    return fail(AMQFT_ERR_ALIGN, "amqft_exec_dct_dst: give both or neither of dct_in/dct_out, dst_in/dst_out");
+  if (count == 0 || (!dct_in && !dst_in)) return AMQFT_OK;
+  if (((uintptr_t)dct_in | (uintptr_t)dct_out | (uintptr_t)dst_in | (uintptr_t)dst_out) & 3u)
+    return fail(AMQFT_ERR_ALIGN, "amqft_exec_dct_dst: arrays must be 4-byte aligned");
+  const long long half = 1LL << (p->log2n - 1);
+  const uintptr_t cb = (uintptr_t)((half + 1) * count * 4), sb = (uintptr_t)((half - 1) * count * 4);
+  const uintptr_t ci = (uintptr_t)dct_in, co = (uintptr_t)dct_out, si = (uintptr_t)dst_in, so = (uintptr_t)dst_out;
+  // each kind may run in place; nothing else may overlap
+  if ((ci != co && ranges_overlap(ci, cb, co, cb)) || (si != so && ranges_overlap(si, sb, so, sb)) ||
+      ranges_overlap(ci, cb, si, sb) || ranges_overlap(ci, cb, so, sb) || ranges_overlap(co, cb, si, sb) ||
+      ranges_overlap(co, cb, so, sb))
+    return fail(AMQFT_ERR_INPLACE, "amqft_exec_dct_dst: arrays overlap");
+  return exec_special(p, SP_TRIG, count, dct_in, dct_out, dst_in, dst_out, stream, "amqft_exec_dct_dst: launch");
 }
 
 // Host-memory execution: staging on the device, three internal streams.
@@ -737,7 +825,7 @@ int amqft_exec_ragged(amqft_plan_t p, int64_t count, const int64_t* d_offsets, c
     const long long capc = ragged_capacity(p, c);
     if (capc < 1) continue;
     const long long RSg = region_stride_g(c);
-    MpArgs m;
+    MpArgs m = {};
     memset(&m, 0, sizeof m);
     m.in = in;
     m.out = out;

@@ -76,6 +76,16 @@ struct FusedArgs {
   long long nreal;     // > 0: real input, transform t = real signals 2t and 2t+1
                        // (float32, N each, the second absent past nreal); out holds
                        // the N/2 + 1 harmonics of every signal (forward only)
+  long long ntrig;     // > 0: DCT-0 / DST-0 (Eq. qft_0B-0C) of ntrig signals of each
+                       // kind, transform t = signals 2t and 2t+1: regions C1 / C2 take
+                       // DCT-0 inputs (in: N/2 + 1 floats each, n = 0..N/2), S1 / S2
+                       // DST-0 inputs (in2: N/2 - 1 floats, n = 1..N/2-1 at [n-1]);
+                       // results alike at out / out2 (a NULL pair: that kind absent)
+  const float* in2;
+  float* out2;
+  long long nirdft;    // > 0: inverse real transform of nirdft half spectra (in:
+                       // N/2 + 1 complex64 each), transform t = spectra 2t and 2t+1 as
+                       // Z = X_a + i X_b; out: the real signals, N floats each
 };
 
 template <int V>

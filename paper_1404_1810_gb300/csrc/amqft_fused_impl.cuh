@@ -152,53 +152,131 @@ __device__ __forceinline__ Fetched load_fetch_real(const float* __restrict__ in,
   return f;
 }
 
+// Inverse real transform, orbit item n of transform t: the complex samples of
+// Z = X_a + i X_b at n, N - n, N/2 - n, N/2 + n (item 0: 0, N/2, N/4, 3N/4),
+// from the half spectra of signals 2t and 2t + 1 (Hermitian symmetry,
+// X(N - j) = conj X(j)), conjugated (the inverse is conj F conj).
+__device__ __forceinline__ Fetched load_fetch_irdft(const float2* __restrict__ in, int logN, long long t,
+                                                    long long nsig, int n) {
+  const int N = 1 << logN, half = N >> 1, Q = N >> 2;
+  const float2* __restrict__ xa = in + (2 * t) * (long long)(half + 1);
+  const float2* __restrict__ xb = xa + (half + 1);
+  const bool hb = 2 * t + 1 < nsig;
+  // conj(Z(j)) and conj(Z(N - j)) from X_a(j), X_b(j), 0 <= j <= N/2
+  auto pair = [&](int j, float2& zj, float2& zmj) {
+    const float2 A = __ldcs(xa + j), B = hb ? __ldcs(xb + j) : make_float2(0.f, 0.f);
+    zj = make_float2(A.x - B.y, -(A.y + B.x));
+    zmj = make_float2(A.x + B.y, -(B.x - A.y));
+  };
+  Fetched f;
+  float2 u;
+  if (n == 0) {
+    pair(0, f.a, u);
+    pair(half, f.b, u);
+    if (N >= 4) pair(Q, f.c, f.d);
+  } else {
+    pair(n, f.a, f.b);
+    pair(half - n, f.c, f.d);
+  }
+  return f;
+}
+
+// The D_r outputs of orbit item n for the two real signals of a transform
+// (channel 1: the real parts, regions C1 / S1; channel 2: the imaginary
+// parts, C2 / S2).  n > 0: a = dc(n), b = ds(n), c = dc(N/2-n), d = ds(N/2-n);
+// n = 0: a = dc(0), b = dc(N/2), c = dc(N/4), d = ds(N/4) (N = 2: a, b only).
+struct DrItem {
+  float a1, b1, c1, d1, a2, b2, c2, d2;
+};
+
+// D_r (Eq. qft_22-23) on the four complex samples of item n:
+// dc(n) = x(n) + x(N-n), ds(n) = x(n) - x(N-n); dc(0) = x(0), dc(N/2) = x(N/2).
+__device__ __forceinline__ DrItem d_r(const Fetched& f, int N, int n) {
+  DrItem r;
+  if (n == 0) {
+    r.a1 = f.a.x; r.b1 = f.b.x; r.a2 = f.a.y; r.b2 = f.b.y;
+    if (N >= 4) {
+      r.c1 = f.c.x + f.d.x; r.d1 = f.c.x - f.d.x; r.c2 = f.c.y + f.d.y; r.d2 = f.c.y - f.d.y;
+    } else {
+      r.c1 = r.d1 = r.c2 = r.d2 = 0.f;
+    }
+    return r;
+  }
+  r.a1 = f.a.x + f.b.x; r.b1 = f.a.x - f.b.x; r.c1 = f.c.x + f.d.x; r.d1 = f.c.x - f.d.x;
+  r.a2 = f.a.y + f.b.y; r.b2 = f.a.y - f.b.y; r.c2 = f.c.y + f.d.y; r.d2 = f.c.y - f.d.y;
+  return r;
+}
+
+// DCT-0 / DST-0 mode, orbit item n of transform t: the regions' inputs are
+// the caller's signals themselves (no D_c, D_r).  Signals 2t (channel 1) and
+// 2t + 1 (channel 2) of each kind; absent ones read as zero.
+__device__ __forceinline__ DrItem load_fetch_trig(const float* __restrict__ dct, const float* __restrict__ dst,
+                                                  long long ntrig, int logN, long long t, int n) {
+  const int N = 1 << logN, half = N >> 1, Q = N >> 2;
+  const long long s1 = 2 * t, s2 = 2 * t + 1;
+  const long long c1 = s1 * (half + 1), c2 = s2 * (half + 1);  // DCT-0 input n at c + n
+  const long long d1 = s1 * (half - 1) - 1, d2 = s2 * (half - 1) - 1;  // DST-0 input n at d + n
+  const bool h1 = s1 < ntrig, h2 = s2 < ntrig;
+  auto C = [&](bool ok, long long i) { return ok && dct ? __ldcs(dct + i) : 0.f; };
+  auto S = [&](bool ok, long long i) { return ok && dst ? __ldcs(dst + i) : 0.f; };
+  DrItem r;
+  if (n == 0) {
+    r.a1 = C(h1, c1); r.b1 = C(h1, c1 + half); r.c1 = C(h1, c1 + Q); r.d1 = S(h1, d1 + Q);
+    r.a2 = C(h2, c2); r.b2 = C(h2, c2 + half); r.c2 = C(h2, c2 + Q); r.d2 = S(h2, d2 + Q);
+    return r;
+  }
+  r.a1 = C(h1, c1 + n); r.b1 = S(h1, d1 + n); r.c1 = C(h1, c1 + half - n); r.d1 = S(h1, d1 + half - n);
+  r.a2 = C(h2, c2 + n); r.b2 = S(h2, d2 + n); r.c2 = C(h2, c2 + half - n); r.d2 = S(h2, d2 + half - n);
+  return r;
+}
+
+// Place item n's DCT-0 / DST-0 inputs in the four regions (chain layout; the
+// harmonics-first variants also take the first D_k of the chain here).
 template <int V, class RG>
-__device__ __forceinline__ void load_scatter(const RG& rg, int logN, int tau, int n, const Fetched& f) {
+__device__ __forceinline__ void load_place(const RG& rg, int logN, int tau, int n, const DrItem& r) {
   const int N = 1 << logN, half = N >> 1, Q = N >> 2, logQ = logN - 2;
   float* C1 = rg.get(tau, 0);
   float* S1 = rg.get(tau, 1);
   float* C2 = rg.get(tau, 2);
   float* S2 = rg.get(tau, 3);
   if (n == 0) {
-    const float2 z0 = f.a, zh = f.b;
     if (N == 2) {
-      C1[0] = z0.x; C1[1] = zh.x; C2[0] = z0.y; C2[1] = zh.y;
+      C1[0] = r.a1; C1[1] = r.b1; C2[0] = r.a2; C2[1] = r.b2;
       return;
     }
-    const float2 zq = f.c, z3 = f.d;
-    const float cq1 = zq.x + z3.x, sq1 = zq.x - z3.x, cq2 = zq.y + z3.y, sq2 = zq.y - z3.y;
     if constexpr (Var<V>::ot) {
-      C1[sw(half - 1)] = z0.x; C1[sw(half)] = zh.x;
-      C2[sw(half - 1)] = z0.y; C2[sw(half)] = zh.y;
-      C1[sw(half - 2)] = cq1; C2[sw(half - 2)] = cq2;   // pos_chain(Q, dct) = half - 2
-      S1[sw(half - 2)] = sq1; S2[sw(half - 2)] = sq2;   // dst(4) base
+      C1[sw(half - 1)] = r.a1; C1[sw(half)] = r.b1;
+      C2[sw(half - 1)] = r.a2; C2[sw(half)] = r.b2;
+      C1[sw(half - 2)] = r.c1; C2[sw(half - 2)] = r.c2;   // pos_chain(Q, dct) = half - 2
+      S1[sw(half - 2)] = r.d1; S2[sw(half - 2)] = r.d2;   // dst(4) base
     } else {
-      C1[sw(Q)] = z0.x + zh.x; C1[sw(0)] = z0.x - zh.x;   // te(0), to(0)
-      C2[sw(Q)] = z0.y + zh.y; C2[sw(0)] = z0.y - zh.y;
-      C1[sw(half)] = cq1; C2[sw(half)] = cq2;           // te(Q) = dc(Q)
-      S1[sw(Q - 1)] = sq1; S2[sw(Q - 1)] = sq2;         // to(Q) = ds(Q)
+      C1[sw(Q)] = r.a1 + r.b1; C1[sw(0)] = r.a1 - r.b1;   // te(0), to(0)
+      C2[sw(Q)] = r.a2 + r.b2; C2[sw(0)] = r.a2 - r.b2;
+      C1[sw(half)] = r.c1; C2[sw(half)] = r.c2;           // te(Q) = dc(Q)
+      S1[sw(Q - 1)] = r.d1; S2[sw(Q - 1)] = r.d2;         // to(Q) = ds(Q)
     }
     return;
   }
   const int m = half - n;
-  const float2 za = f.a, zb = f.b, zc = f.c, zd = f.d;
-  // D_r: dc(n) = x(n) + x(N-n), ds(n) = x(n) - x(N-n), for n and N/2 - n
-  const float dcn1 = za.x + zb.x, dsn1 = za.x - zb.x, dcm1 = zc.x + zd.x, dsm1 = zc.x - zd.x;
-  const float dcn2 = za.y + zb.y, dsn2 = za.y - zb.y, dcm2 = zc.y + zd.y, dsm2 = zc.y - zd.y;
   if constexpr (Var<V>::ot) {
     const int pcn = sw(pos_chain(n, logN, 0)), pcm = sw(pos_chain(m, logN, 0));
     const int psn = sw(pos_chain(n, logN, 1)), psm = sw(pos_chain(m, logN, 1));
-    C1[pcn] = dcn1; C1[pcm] = dcm1; S1[psn] = dsn1; S1[psm] = dsm1;
-    C2[pcn] = dcn2; C2[pcm] = dcm2; S2[psn] = dsn2; S2[psm] = dsm2;
+    C1[pcn] = r.a1; C1[pcm] = r.c1; S1[psn] = r.b1; S1[psm] = r.d1;
+    C2[pcn] = r.a2; C2[pcm] = r.c2; S2[psn] = r.b2; S2[psm] = r.d2;
   } else {
     // first D_k of the chain (M = N): te -> dct(N/2), to -> dct_to(N) bit-reversed
     const int pte = sw(Q + n), pto = sw(brev(n, logQ));
     const int ste = sw(Q + n - 1), sto = sw(brev(n - 1, logQ));
-    C1[pte] = dcn1 + dcm1; C1[pto] = dcn1 - dcm1;
-    C2[pte] = dcn2 + dcm2; C2[pto] = dcn2 - dcm2;
-    S1[ste] = dsn1 - dsm1; S1[sto] = dsn1 + dsm1;
-    S2[ste] = dsn2 - dsm2; S2[sto] = dsn2 + dsm2;
+    C1[pte] = r.a1 + r.c1; C1[pto] = r.a1 - r.c1;
+    C2[pte] = r.a2 + r.c2; C2[pto] = r.a2 - r.c2;
+    S1[ste] = r.b1 - r.d1; S1[sto] = r.b1 + r.d1;
+    S2[ste] = r.b2 - r.d2; S2[sto] = r.b2 + r.d2;
   }
+}
+
+template <int V, class RG>
+__device__ __forceinline__ void load_scatter(const RG& rg, int logN, int tau, int n, const Fetched& f) {
+  load_place<V>(rg, logN, tau, n, d_r(f, 1 << logN, n));
 }
 
 // Store stage for orbit item k: harmonics k, N-k, N/2-k, N/2+k (item 0:
@@ -565,6 +643,58 @@ __device__ __forceinline__ void region_to_natural(float* R, int ctx) {
   }
 }
 
+// DCT-0 / DST-0 mode, orbit item k: the regions' own results (no D_r^F,
+// D_c^F) at harmonics k and N/2 - k (item 0: 0, N/2, N/4) to the DCT-0 and
+// DST-0 outputs of signals 2t and 2t + 1.
+template <int V>
+__device__ __forceinline__ void store_trig(float* __restrict__ dct, float* __restrict__ dst, long long ntrig,
+                                           int logN, long long t, int k, const Gathered& g) {
+  const int N = 1 << logN, half = N >> 1, Q = N >> 2;
+  const long long s1 = 2 * t, s2 = 2 * t + 1;
+  const long long c1 = s1 * (half + 1), c2 = s2 * (half + 1);
+  const long long d1 = s1 * (half - 1) - 1, d2 = s2 * (half - 1) - 1;
+  const bool h1 = s1 < ntrig, h2 = s2 < ntrig;
+  auto C = [&](bool ok, long long i, float v) { if (ok && dct) __stcs(dct + i, v); };
+  auto S = [&](bool ok, long long i, float v) { if (ok && dst) __stcs(dst + i, v); };
+  float ck1, ck2, cm1, cm2, sk1, sk2, sm1, sm2;
+  if constexpr (Var<V>::ot) {  // last D_n of the chain (M = N)
+    ck1 = g.v[0] + g.v[1]; cm1 = g.v[0] - g.v[1]; ck2 = g.v[2] + g.v[3]; cm2 = g.v[2] - g.v[3];
+  } else {
+    ck1 = g.v[0]; cm1 = g.v[1]; ck2 = g.v[2]; cm2 = g.v[3];
+  }
+  if (k == 0) {  // C(0) = ck, C(N/2) = cm, C(N/4) and S(N/4) as gathered
+    C(h1, c1, ck1); C(h1, c1 + half, cm1); C(h1, c1 + Q, g.v[4]); S(h1, d1 + Q, g.v[6]);
+    C(h2, c2, ck2); C(h2, c2 + half, cm2); C(h2, c2 + Q, g.v[5]); S(h2, d2 + Q, g.v[7]);
+    return;
+  }
+  if constexpr (Var<V>::ot) {
+    sk1 = g.v[4] + g.v[5]; sm1 = g.v[4] - g.v[5]; sk2 = g.v[6] + g.v[7]; sm2 = g.v[6] - g.v[7];
+  } else {
+    sk1 = g.v[4]; sm1 = g.v[5]; sk2 = g.v[6]; sm2 = g.v[7];
+  }
+  C(h1, c1 + k, ck1); C(h1, c1 + half - k, cm1); S(h1, d1 + k, sk1); S(h1, d1 + half - k, sm1);
+  C(h2, c2 + k, ck2); C(h2, c2 + half - k, cm2); S(h2, d2 + k, sk2); S(h2, d2 + half - k, sm2);
+}
+
+// Inverse real transform, orbit item k: the up to four outputs of the
+// complex inverse of Z = X_a + i X_b; their real parts are N x_a, their
+// imaginary parts N x_b (signals 2t and 2t + 1, N floats each).
+template <int V>
+__device__ __forceinline__ void store_irdft(float* __restrict__ out, long long nsig, int logN, long long t, int k,
+                                            const Gathered& g, float cj) {
+  const int N = 1 << logN;
+  float* __restrict__ xa = out + (2 * t) * (long long)N;
+  float* __restrict__ xb = xa + N;
+  const bool hb = 2 * t + 1 < nsig;
+  const Out4 o = emit_values<V>(logN, k, g);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    if (o.i[i] < 0) continue;
+    __stcs(xa + o.i[i], o.v[i].x);
+    if (hb) __stcs(xb + o.i[i], o.v[i].y * cj);
+  }
+}
+
 // Stage 2, across the cluster: D_r^F (Eq. qft_24-25: Re R = DCT, Im R = -DST)
 // and D_c^F (Eq. qft_17-21) for four consecutive harmonics per step, the four
 // regions read as float4 through distributed shared memory:
@@ -578,6 +708,20 @@ __device__ __forceinline__ void store_natural_cluster(float* sm, const FusedArgs
   static_assert(NG * 4 * TPB == PER, "four harmonics per thread and step");
   cg::cluster_group cl = cg::this_cluster();
   const int rank = (int)cl.block_rank();
+  if (a.ntrig > 0) {
+    // DCT-0 / DST-0 mode: each CTA writes its own region, in natural order
+    const long long sig = 2 * t + (rank >> 1);
+    if (sig < a.ntrig) {
+      if ((rank & 1) == 0 && a.out) {
+        float* __restrict__ o = static_cast<float*>(a.out) + sig * (long long)(half + 1);
+        for (int k = (int)threadIdx.x; k <= half; k += TPB) __stcs(o + k, sm[k]);
+      } else if ((rank & 1) == 1 && a.out2) {
+        float* __restrict__ o = a.out2 + sig * (long long)(half - 1) - 1;
+        for (int k = 1 + (int)threadIdx.x; k < half; k += TPB) __stcs(o + k, sm[k]);
+      }
+    }
+    return;
+  }
   if (a.nreal > 0) {
     // real input: R = DCT - i DST of each signal of the pair, harmonics 0 .. N/2
     float2* __restrict__ ra = static_cast<float2*>(a.out) + (2 * t) * (long long)(half + 1);
@@ -618,6 +762,28 @@ __device__ __forceinline__ void store_natural_cluster(float* sm, const FusedArgs
     }
     return k0;
   };
+  if (a.nirdft > 0) {
+    // inverse real transform: Re -> signal 2t, Im -> signal 2t + 1
+    float* __restrict__ xa = static_cast<float*>(a.out) + (2 * t) * (long long)N;
+    float* __restrict__ xb = xa + N;
+    const bool hb = 2 * t + 1 < a.nirdft;
+#pragma unroll
+    for (int gi = 0; gi < NG; ++gi) {
+      float2 f[4], b[4];
+      const int k0 = group(gi, f, b);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        const int kb = k0 == 0 && i == 0 ? half : N - k0 - i;
+        __stcs(xa + k0 + i, f[i].x);
+        __stcs(xa + kb, b[i].x);
+        if (hb) {
+          __stcs(xb + k0 + i, f[i].y * cj);
+          __stcs(xb + kb, b[i].y * cj);
+        }
+      }
+    }
+    return;
+  }
   if (a.dtype == DT_C64) {
     float2* __restrict__ z = static_cast<float2*>(a.out) + off;
     const bool vec_ok = (reinterpret_cast<uintptr_t>(z) & 15u) == 0;  // same for every thread
@@ -841,7 +1007,7 @@ __device__ __forceinline__ void fused_body(const FusedArgs& a, const SmallConsts
   for (int rd = 0; rd < NR; ++rd) {
     int n_[U], tau_[U];
     bool ok_[U];
-    Fetched f_[U];
+    DrItem r_[U];
 #pragma unroll
     for (int s = 0; s < U; ++s) {
       const int idx = rd * U + s;
@@ -858,13 +1024,20 @@ __device__ __forceinline__ void fused_body(const FusedArgs& a, const SmallConsts
       }
       if (ok_[s]) {
         const long long t = tid(tau_[s]);
-        f_[s] = a.nreal > 0 ? load_fetch_real(static_cast<const float*>(a.in), logN, t, a.nreal, n_[s])
-                            : load_fetch(InRef{a.in, a.exp_in, a.dtype}, logN, t, toff(t), n_[s], cj);
+        if (a.ntrig > 0) {
+          r_[s] = load_fetch_trig(static_cast<const float*>(a.in), a.in2, a.ntrig, logN, t, n_[s]);
+        } else {
+          const Fetched f =
+              a.nreal > 0 ? load_fetch_real(static_cast<const float*>(a.in), logN, t, a.nreal, n_[s])
+              : a.nirdft > 0 ? load_fetch_irdft(static_cast<const float2*>(a.in), logN, t, a.nirdft, n_[s])
+                             : load_fetch(InRef{a.in, a.exp_in, a.dtype}, logN, t, toff(t), n_[s], cj);
+          r_[s] = d_r(f, N, n_[s]);
+        }
       }
     }
 #pragma unroll
     for (int s = 0; s < U; ++s)
-      if (ok_[s]) load_scatter<V>(rg, logN, tau_[s], n_[s], f_[s]);
+      if (ok_[s]) load_place<V>(rg, logN, tau_[s], n_[s], r_[s]);
   }
   if constexpr (CL == 1) __syncthreads();
   else cg::this_cluster().sync();
@@ -940,7 +1113,11 @@ __device__ __forceinline__ void fused_body(const FusedArgs& a, const SmallConsts
       for (int s = 0; s < U; ++s) {
         if (!ok_[s]) continue;
         const long long t = tid(tau_[s]);
-        if (a.nreal > 0) {
+        if (a.ntrig > 0) {
+          store_trig<V>(static_cast<float*>(a.out), a.out2, a.ntrig, logN, t, k_[s], g_[s]);
+        } else if (a.nirdft > 0) {
+          store_irdft<V>(static_cast<float*>(a.out), a.nirdft, logN, t, k_[s], g_[s], cj);
+        } else if (a.nreal > 0) {
           store_real<V>(static_cast<float2*>(a.out), logN, t, a.nreal, k_[s], g_[s]);
         } else if (c64) {
           store_emit<V>(static_cast<float2*>(a.out), logN, toff(t), k_[s], g_[s], cj);

@@ -46,6 +46,12 @@ struct MpArgs {
   const int* tlist;   // transform ids of chunk positions (NULL: t0 + position)
   const long long* toff;  // element offset of each transform id (NULL: id * N)
   const int* ntdev;   // transforms in this chunk, read on the device (NULL: nt); nt is then the capacity
+  // special input / output forms (all 0: complex): transform id t = signals 2t, 2t + 1
+  long long nreal;    // real input (in: N floats a signal), half spectra out (N/2 + 1 complex64)
+  long long ntrig;    // DCT-0 / DST-0: in / out the DCT-0 signals, in2 / out2 the DST-0 ones
+  long long nirdft;   // half spectra in, real signals out (inverse)
+  const float* in2;
+  float* out2;
 };
 
 __device__ __forceinline__ long long mp_nt(const MpArgs& a) {
@@ -78,8 +84,16 @@ __global__ void mp_load_kernel(MpArgs a, float* W) {
     const long long t = w >> logQ;
     const int n = (int)(w & ((1LL << logQ) - 1));
     const long long id = mp_id(a, t);
-    const Fetched f = load_fetch(InRef{a.in, a.exp_in, a.dtype}, a.logN, id, mp_off(a, id), n, cj);
-    load_scatter<V>(rg, a.logN, (int)t, n, f);
+    if (a.ntrig > 0) {
+      load_place<V>(rg, a.logN, (int)t, n,
+                    load_fetch_trig(static_cast<const float*>(a.in), a.in2, a.ntrig, a.logN, id, n));
+    } else {
+      const Fetched f =
+          a.nreal > 0 ? load_fetch_real(static_cast<const float*>(a.in), a.logN, id, a.nreal, n)
+          : a.nirdft > 0 ? load_fetch_irdft(static_cast<const float2*>(a.in), a.logN, id, a.nirdft, n)
+                         : load_fetch(InRef{a.in, a.exp_in, a.dtype}, a.logN, id, mp_off(a, id), n, cj);
+      load_scatter<V>(rg, a.logN, (int)t, n, f);
+    }
   }
 }
 
@@ -93,7 +107,11 @@ __global__ void mp_store_kernel(MpArgs a, const float* W) {
     const long long t = w >> logQ;
     const int k = (int)(w & ((1LL << logQ) - 1));
     const Gathered g = store_gather<V>(rg, a.logN, (int)t, k);
-    store_emit<V>(static_cast<float2*>(a.out), a.logN, mp_off(a, mp_id(a, t)), k, g, cj);
+    const long long id = mp_id(a, t);
+    if (a.ntrig > 0) store_trig<V>(static_cast<float*>(a.out), a.out2, a.ntrig, a.logN, id, k, g);
+    else if (a.nirdft > 0) store_irdft<V>(static_cast<float*>(a.out), a.nirdft, a.logN, id, k, g, cj);
+    else if (a.nreal > 0) store_real<V>(static_cast<float2*>(a.out), a.logN, id, a.nreal, k, g);
+    else store_emit<V>(static_cast<float2*>(a.out), a.logN, mp_off(a, id), k, g, cj);
   }
 }
 

@@ -93,7 +93,7 @@ extern "C" int amqft_exec_static(amqft_plan_t plan, int64_t batch, const void* i
   const long long chunk = AMQFT_STATIC_SCRATCH_FLOATS / per_t;  // >= 2 for log2n <= AMQFT_STATIC_LOG2N_MAX
   cudaStream_t st = (cudaStream_t)stream;
   for (long long t0 = 0; t0 < batch; t0 += chunk) {
-    MpArgs a;
+    MpArgs a = {};
     a.in = in;
     a.out = out;
     a.exp_in = nullptr;

@@ -1,5 +1,5 @@
 """Real input (amqft_exec_rdft): pairs of real signals share one complex
-transform.  Every harmonic 0 .. N/2 must equal the complex transform of the
+transform, on the fused kernels and (above 2^16) the multi-pass path.  Every harmonic 0 .. N/2 must equal the complex transform of the
 signal with a zero imaginary part (same kernels, same float32 operations),
 and the float64 reference within the float32 recursion's error."""
 import numpy as np
@@ -63,15 +63,21 @@ def test_rdft_against_float64(orc, log2n, v):
         assert rel(r[i], ref) <= derived_tol(rel(r32, ref), log2n)
 
 
-def test_rdft_rejects_what_it_does_not_cover():
+@pytest.mark.parametrize("log2n,v", [(17, 4), (18, 1), (17, 6)])
+def test_rdft_multipass_equals_complex_path(log2n, v):
+    """Above 2^16 the real input runs on the multi-pass path: still every
+    harmonic of the complex transform of the zero-imaginary signal."""
     import torch
 
-    from paper_1404_1810_gb300 import AmqftError, Plan
+    from paper_1404_1810_gb300 import Plan
 
-    p = Plan(17, 4, 1)
+    n, b = 1 << log2n, 3
+    xr = torch.from_numpy(synth.real_signals(n, b, stream=log2n + 10 * v).astype(np.float32)).cuda()
+    p = Plan(log2n, v, b)
     try:
-        with pytest.raises(AmqftError) as e:
-            p.rdft(torch.zeros(1 << 17, dtype=torch.float32, device="cuda"))
-        assert e.value.code == -1
+        r = p.rdft(xr)
+        full = p.fwd(torch.complex(xr, torch.zeros_like(xr)).contiguous())
+        torch.cuda.synchronize()
+        assert torch.equal(r, full[:, : n // 2 + 1]), (log2n, v)
     finally:
         p.close()

@@ -58,7 +58,7 @@ def parse_args():
                     help="c2 (default): the batched complex64 forward+inverse line; c1: N=1024 latency of "
                          "all variants; c3: 16-bit storage; c4: ragged batch in one CUDA graph; c5: autograd "
                          "forward+backward")
-    ap.add_argument("--dtype16", default="bf16", choices=["bf16", "fp16"])
+    ap.add_argument("--dtype16", default="bf16", choices=["bf16", "fp16", "i16"])
     ap.add_argument("--constants", default="table", choices=["table", "fly", "auto"],
                     help="band-level trig constants: the plan's table, evaluated on the fly in the kernels, or "
                          "whichever the autotuner times faster on this workload")
@@ -417,12 +417,14 @@ def run_extra(args):
         import oracle
 
         oracle.build()
-        dt = 1 if args.dtype16 == "bf16" else 2
-        tdt = torch.bfloat16 if dt == 1 else torch.float16
+        dt = {"bf16": 1, "fp16": 2, "i16": 3}[args.dtype16]
+        tdt = {1: torch.bfloat16, 2: torch.float16, 3: torch.int16}[dt]
         log2n = args.log2n
         n = 1 << log2n
         batch = 1 << (27 - log2n)
-        x = torch.view_as_real(synth.device_normal_complex64(n, batch, dev)).to(tdt).contiguous()
+        x = torch.view_as_real(synth.device_normal_complex64(n, batch, dev))
+        # int16 block floating point: the signal times 2^12 as integers, exponent 0
+        x = (x * 4096.0).round().to(tdt).contiguous() if dt == 3 else x.to(tdt).contiguous()
         y, z = torch.empty_like(x), torch.empty_like(x)
         ey = torch.empty(batch, dtype=torch.int32, device=dev)
         ez = torch.empty(batch, dtype=torch.int32, device=dev)
@@ -452,7 +454,8 @@ def run_extra(args):
                 "higher_is_better": True, "n_gpus": 1, "steps": K, "warmup": W, "dtype": f"{args.dtype16}-storage",
                 "data": "synthetic",
                 "config": {"workload": f"16-bit storage forward+inverse, N=2^{log2n}, batch {batch} (2^27 points), "
-                                       f"Re/Im iid N(0,1) rounded to {args.dtype16}", "variant": args.variant,
+                                       f"Re/Im iid N(0,1){' x 2^12' if dt == 3 else ''} rounded to {args.dtype16}",
+                           "variant": args.variant,
                            "l2": "inputs larger than L2"},
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": None, "peak_kind": kind,

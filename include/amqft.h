@@ -13,14 +13,17 @@
  *   - Data are interleaved complex (re, im), transform-major: transform b
  *     occupies elements [b*N, (b+1)*N).  AMQFT_C64 elements are 2 x float32
  *     (8 bytes); in and out must be 8-byte aligned device pointers.
- *   - 16-bit storage (AMQFT_CBF16, AMQFT_CF16): an element is a pair of
- *     bfloat16 or IEEE binary16 values (4 bytes, real part first), in and out
- *     4-byte aligned.  Transform b holds the values stored * 2^exp[b], one
+ *   - 16-bit storage (AMQFT_CBF16, AMQFT_CF16, AMQFT_CI16): an element is a
+ *     pair of bfloat16, IEEE binary16 or int16 values (4 bytes, real part
+ *     first), in and out 4-byte aligned; int16 is block-floating point
+ *     (fixed-point mantissas with one exponent per transform, 15 bits below
+ *     the largest component; the paper's fixed-point motivation, with the
+ *     arithmetic kept in float32).  Transform b holds the values stored * 2^exp[b], one
  *     int32 exponent per transform in a separate device array.  Arithmetic is
  *     float32 throughout: inputs are widened and scaled exactly; each output
  *     transform gets the exponent that puts its largest component magnitude
  *     in [2^13, 2^14) (0 for an all-zero transform), is scaled by 2^-exp
- *     exactly and rounded once to nearest even.  Exponents are clamped to
+ *     exactly and rounded once to nearest even (int16: to the nearest integer, ties to even).  Exponents are clamped to
  *     [-100, 100] (outside that range the scaling saturates).
  *   - in and out are owned by the caller.  in == out is the in-place
  *     transform (every entry point but amqft_exec_rdft / amqft_exec_irdft;
@@ -61,7 +64,7 @@ extern "C" {
 #define AMQFT_LOG2N_FUSED_MAX 16 /* largest log2n of the fused single-pass kernels */
 #define AMQFT_LOG2N_MAX 28       /* largest log2n (multi-pass above 2^16) */
 
-typedef enum { AMQFT_C64 = 0, AMQFT_CBF16 = 1, AMQFT_CF16 = 2 } amqft_dtype;
+typedef enum { AMQFT_C64 = 0, AMQFT_CBF16 = 1, AMQFT_CF16 = 2, AMQFT_CI16 = 3 } amqft_dtype;
 
 typedef struct amqft_plan_s *amqft_plan_t;
 
@@ -206,6 +209,20 @@ int amqft_plan_set_constants(amqft_plan_t plan, int mode);
 
 /* The plan's constants mode, or AMQFT_ERR_ARG for a NULL plan. */
 int amqft_plan_get_constants(amqft_plan_t plan);
+
+/* Bounds checks.  The debug library (libamqft_debug.so, the same sources
+ * built with AMQFT_BOUNDS_CHECK) checks every region access of the kernels
+ * (shared memory, the cluster's distributed shared memory, the multi-pass
+ * workspace) against the region's size, the paired kernel's region and HBM
+ * accesses, and the HBM element index of every input and output against the
+ * transform length.  A failing access is skipped (a load reads zero or a
+ * scratch word, a store is dropped), counted, and the first one recorded as
+ * (site << 48) | (index & (2^48 - 1)); nothing traps, so the kernel ends and
+ * the context stays usable.  This call reads (and if `clear` is nonzero
+ * resets) the record; it synchronises with the device's work through the
+ * copy.  Returns 1 in the checked build, 0 in the release build (whose count
+ * is always 0), or AMQFT_ERR_CUDA.  count / first may be NULL. */
+int amqft_debug_bounds(int64_t *count, uint64_t *first, int clear);
 
 /* ---------------------------------------------------------------------
  * Ragged batches: many transforms of different power-of-two lengths, each at

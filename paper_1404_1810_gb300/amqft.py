@@ -12,7 +12,7 @@ import threading
 
 from . import build as _build
 
-AMQFT_C64, AMQFT_CBF16, AMQFT_CF16 = 0, 1, 2
+AMQFT_C64, AMQFT_CBF16, AMQFT_CF16, AMQFT_CI16 = 0, 1, 2, 3
 ERRORS = {
     -1: "AMQFT_ERR_N", -2: "AMQFT_ERR_VARIANT", -3: "AMQFT_ERR_DTYPE", -4: "AMQFT_ERR_ALIGN",
     -5: "AMQFT_ERR_INPLACE", -6: "AMQFT_ERR_CUDA", -7: "AMQFT_ERR_DEVICE", -8: "AMQFT_ERR_ARG",
@@ -77,8 +77,41 @@ def load(path: str | None = None) -> ctypes.CDLL:
         lib.amqft_plan_set_constants.restype = i32
         lib.amqft_plan_get_constants.argtypes = [vp]
         lib.amqft_plan_get_constants.restype = i32
+        lib.amqft_debug_bounds.argtypes = [ctypes.POINTER(i64), ctypes.POINTER(ctypes.c_uint64), i32]
+        lib.amqft_debug_bounds.restype = i32
         _lib = lib
         return lib
+
+
+class use_library:
+    """Context manager: every binding call inside uses the library at `path`
+    (e.g. the bounds-checked build), the previous one again afterwards.
+    Plans must not cross the boundary."""
+
+    def __init__(self, path: str):
+        self.path = path
+
+    def __enter__(self):
+        global _lib
+        self.saved = load()
+        with _lock:
+            _lib = None
+        return load(self.path)
+
+    def __exit__(self, *exc):
+        global _lib
+        with _lock:
+            _lib = self.saved
+        return False
+
+
+def amqft_debug_bounds(clear: bool = False) -> tuple[bool, int, int]:
+    """(checked build?, failures, first failure) of the loaded library."""
+    c, f = ctypes.c_int64(0), ctypes.c_uint64(0)
+    rc = int(load().amqft_debug_bounds(ctypes.byref(c), ctypes.byref(f), 1 if clear else 0))
+    if rc < 0:
+        _check(rc, "amqft_debug_bounds")
+    return rc == 1, int(c.value), int(f.value)
 
 
 def _check(rc: int, where: str) -> None:
@@ -203,15 +236,16 @@ def _stream_handle(stream) -> int:
     return int(stream.cuda_stream)
 
 
-_TORCH_16 = {AMQFT_CBF16: "bfloat16", AMQFT_CF16: "float16"}
+_TORCH_16 = {AMQFT_CBF16: "bfloat16", AMQFT_CF16: "float16", AMQFT_CI16: "int16"}
 
 
 class Plan:
     """Owns one amqft plan.
 
     complex64 plans: fwd/inv take and return contiguous complex64 CUDA
-    tensors of shape (batch, N).  16-bit plans (AMQFT_CBF16, AMQFT_CF16):
-    tensors of shape (batch, N, 2) in bfloat16 / float16 (real, imaginary),
+    tensors of shape (batch, N).  16-bit plans (AMQFT_CBF16, AMQFT_CF16,
+    AMQFT_CI16): tensors of shape (batch, N, 2) in bfloat16 / float16 / int16
+    (real, imaginary),
     plus one int32 exponent per transform: fwd(x) returns (y, exp_y) and
     inv(x, exp_x) returns (y, exp_y), the values being y * 2^exp_y."""
 

@@ -324,8 +324,9 @@ int amqft_plan(amqft_plan_t* out, int log2n, int variant, int64_t batch, int dty
   if (log2n < 0 || log2n > AMQFT_LOG2N_MAX)
     return fail(AMQFT_ERR_N, "amqft_plan: log2n=%d outside [0, %d]", log2n, AMQFT_LOG2N_MAX);
   if (variant < 1 || variant > 8) return fail(AMQFT_ERR_VARIANT, "amqft_plan: variant=%d not in 1..8", variant);
-  if (dtype != AMQFT_C64 && dtype != AMQFT_CBF16 && dtype != AMQFT_CF16)
-    return fail(AMQFT_ERR_DTYPE, "amqft_plan: dtype=%d is not AMQFT_C64, AMQFT_CBF16 or AMQFT_CF16", dtype);
+  if (dtype != AMQFT_C64 && dtype != AMQFT_CBF16 && dtype != AMQFT_CF16 && dtype != AMQFT_CI16)
+    return fail(AMQFT_ERR_DTYPE, "amqft_plan: dtype=%d is not AMQFT_C64, AMQFT_CBF16, AMQFT_CF16 or AMQFT_CI16",
+                dtype);
   if (batch < 0) return fail(AMQFT_ERR_ARG, "amqft_plan: batch=%lld < 0", (long long)batch);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -873,6 +874,28 @@ int64_t amqft_plan_launches(amqft_plan_t p) {
   t_err.clear();
   if (!p) return fail(AMQFT_ERR_ARG, "plan is NULL");
   return (int64_t)p->launches.load();
+}
+
+int amqft_debug_bounds(int64_t* count, uint64_t* first, int clear) {
+  t_err.clear();
+  using Reader = cudaError_t (*)(unsigned long long*, unsigned long long*, bool);
+  static const Reader readers[] = {bounds_v1, bounds_v2, bounds_v3, bounds_v4,  bounds_v5, bounds_v6,
+                                   bounds_v7, bounds_v8, bounds_p14, bounds_p15, bounds_p16};
+  unsigned long long total = 0, f = 0;
+  for (Reader r : readers) {
+    unsigned long long c = 0, fi = 0;
+    const cudaError_t e = r(&c, &fi, clear != 0);
+    if (e != cudaSuccess) return cuda_fail(e, "amqft_debug_bounds");
+    if (c && !total) f = fi;
+    total += c;
+  }
+  if (count) *count = (int64_t)total;
+  if (first) *first = (uint64_t)f;
+#ifdef AMQFT_BOUNDS_CHECK
+  return 1;
+#else
+  return 0;
+#endif
 }
 
 int amqft_plan_set_constants(amqft_plan_t p, int mode) {

@@ -55,7 +55,7 @@ __host__ __device__ constexpr int desc_block(int e) {
 
 // ---- ot forward: D_k time phase + M_v time phase over R levels, one item --
 template <int V, int R, int CTX, class CS>
-__device__ __forceinline__ void fold_fwd_item(const float* Rg, int p0, int L, int i, const CS& cs,
+__device__ __forceinline__ void fold_fwd_item(CRegP Rg, int p0, int L, int i, const CS& cs,
                                               float (&x)[1 << R]) {
   constexpr int n = 1 << R;
 #pragma unroll
@@ -75,7 +75,7 @@ __device__ __forceinline__ void fold_fwd_item(const float* Rg, int p0, int L, in
 }
 
 template <int V, int R, int CTX, class CS>
-__device__ __forceinline__ void fold_fwd_pair(float* Rg, int p0, int L, int i, const CS& cs) {
+__device__ __forceinline__ void fold_fwd_pair(RegP Rg, int p0, int L, int i, const CS& cs) {
   const int W = L >> R, i2 = W - 1 - i;
   float x[1 << R], y[1 << R];
   fold_fwd_item<V, R, CTX>(Rg, p0, L, i, cs, x);
@@ -90,7 +90,7 @@ __device__ __forceinline__ void fold_fwd_pair(float* Rg, int p0, int L, int i, c
 
 // ---- to backward: D_n frequency phase + M_v frequency phase, one item -----
 template <int V, int R, int CTX, class CS>
-__device__ __forceinline__ void fold_bwd_item(const float* Rg, int p0, int L, int i, const CS& cs,
+__device__ __forceinline__ void fold_bwd_item(CRegP Rg, int p0, int L, int i, const CS& cs,
                                               float (&x)[1 << R]) {
   constexpr int n = 1 << R;
   const int W = L >> R;
@@ -111,7 +111,7 @@ __device__ __forceinline__ void fold_bwd_item(const float* Rg, int p0, int L, in
 }
 
 template <int V, int R, int CTX, class CS>
-__device__ __forceinline__ void fold_bwd_pair(float* Rg, int p0, int L, int i, const CS& cs) {
+__device__ __forceinline__ void fold_bwd_pair(RegP Rg, int p0, int L, int i, const CS& cs) {
   const int W = L >> R, i2 = W - 1 - i;
   float x[1 << R], y[1 << R];
   fold_bwd_item<V, R, CTX>(Rg, p0, L, i, cs, x);
@@ -124,7 +124,7 @@ __device__ __forceinline__ void fold_bwd_pair(float* Rg, int p0, int L, int i, c
 }
 
 template <int V, bool FWD, int R, class CS>
-__device__ __forceinline__ void fold_pair(float* Rg, int p0, int logL, int i, int ctx, const CS& cs) {
+__device__ __forceinline__ void fold_pair(RegP Rg, int p0, int logL, int i, int ctx, const CS& cs) {
   const int L = 1 << logL;
   if constexpr (FWD) {
     if (ctx == 0) fold_fwd_pair<V, R, 0>(Rg, p0, L, i, cs);
@@ -137,7 +137,7 @@ __device__ __forceinline__ void fold_pair(float* Rg, int p0, int logL, int i, in
 
 // the trees whose roots lie inside the band: root size L >> q, R - q levels
 template <int V, bool FWD, int R, int Q, class CS>
-__device__ __forceinline__ void fold_bundle(float* Rg, int half, int logL, int i, int ctx0, const CS& cs) {
+__device__ __forceinline__ void fold_bundle(RegP Rg, int half, int logL, int i, int ctx0, const CS& cs) {
   if constexpr (Q < R) {
     fold_pair<V, FWD, R - Q>(Rg, half - (2 << (logL - Q)), logL - Q, i, ctx0, cs);
     fold_bundle<V, FWD, R, Q + 1>(Rg, half, logL, i, ctx0, cs);
@@ -158,7 +158,7 @@ __device__ __forceinline__ void run_fold_band(float* sm, const Geo& g, int logL,
   const unsigned stride = GRID ? gridDim.x * TPB : TPB;
   for (unsigned w = start; w < total; w += stride) {
     const unsigned r = dv(w), gidx = w - r * per;
-    float* Rg = sm + (long long)r * g.RS;
+    RegP Rg = reg_ptr(sm + (long long)r * g.RS, g.RS);
     const int c0 = ctx_of(g, r);
     const unsigned b = gidx >> (logW - 1);
     const int i = (int)(gidx & (unsigned)(W2 - 1));
@@ -186,7 +186,7 @@ struct ChunkBwd {
   static constexpr int NDESC = 1 << R;
   // slot: index of the first descendant of this subtree in the snapshot
   template <int SLOT, int NX>
-  __device__ __forceinline__ static void run(const float* Rg, int base, int logL, int m, const Snap& sn, int nslot,
+  __device__ __forceinline__ static void run(CRegP Rg, int base, int logL, int m, const Snap& sn, int nslot,
                                              float (&out)[NX]) {
     if constexpr (R == 0) {
       const int L = 1 << logL;
@@ -245,7 +245,7 @@ struct ChunkBwd {
 // descendant values of one item in snapshot order (the order of the
 // ChunkBwd recursion: A subtree first, then B)
 template <int V, int R, int CTX, int SLOT>
-__device__ __forceinline__ void snap_item(const float* Rg, int base, int logL, int m, float* dst) {
+__device__ __forceinline__ void snap_item(CRegP Rg, int base, int logL, int m, float* dst) {
   if constexpr (R == 0) {
     dst[SLOT] = Rg[sw(base + brev(m, logL))];
   } else {
@@ -257,7 +257,7 @@ __device__ __forceinline__ void snap_item(const float* Rg, int base, int logL, i
 }
 
 template <int V, int R, int CTX>
-__device__ __forceinline__ void chunk_item(float* Rg, int p0, int logL, int m, const Snap& sn, int nslot) {
+__device__ __forceinline__ void chunk_item(RegP Rg, int p0, int logL, int m, const Snap& sn, int nslot) {
   float out[1 << R];
   ChunkBwd<V, R, CTX, 0, 0>::template run<0, (1 << R)>(Rg, p0, logL, m, sn, nslot, out);
   const int lo = m << R;
@@ -268,7 +268,7 @@ __device__ __forceinline__ void chunk_item(float* Rg, int p0, int logL, int m, c
 // items of the trees rooted inside the band, same m for every tree; the
 // snapshot slots of tree q follow those of the trees before it
 template <int V, int R, int Q, int SLOT>
-__device__ __forceinline__ void chunk_bundle(float* Rg, int half, int logL, int m, int ctx0, const Snap& sn,
+__device__ __forceinline__ void chunk_bundle(RegP Rg, int half, int logL, int m, int ctx0, const Snap& sn,
                                              int nslot, bool snap_only, float* dst) {
   if constexpr (Q < R) {
     const int p0 = half - (2 << (logL - Q));
@@ -303,7 +303,7 @@ __device__ __forceinline__ void run_chunk_band(float* sm, float* snap, const Geo
   for (unsigned e = threadIdx.x; e < ends; e += TPB) {
     const unsigned w = ((e >> 1) << 5) | ((e & 1u) ? 31u : 0u);
     const unsigned r = dv(w), it = w - r * per;
-    const float* Rg = sm + (long long)r * g.RS;
+    RegP Rg = reg_ptr(sm + (long long)r * g.RS, g.RS);
     const int c0 = ctx_of(g, r);
     const unsigned b = it >> logW;
     const int m = (int)(it & (unsigned)(W - 1));
@@ -314,14 +314,14 @@ __device__ __forceinline__ void run_chunk_band(float* sm, float* snap, const Geo
       else snap_item<V, R, 1, 0>(Rg, p0, logL, m, dst);
     } else {
       Snap sn{snap, lane, 0};
-      chunk_bundle<V, R, 1, 0>(const_cast<float*>(Rg), g.half, logL, m, c0, sn, NSLOT, true, dst);
+      chunk_bundle<V, R, 1, 0>(Rg, g.half, logL, m, c0, sn, NSLOT, true, dst);
     }
   }
   __syncthreads();
   // pass 2: in place
   for (unsigned w = threadIdx.x; w < total; w += TPB) {
     const unsigned r = dv(w), it = w - r * per;
-    float* Rg = sm + (long long)r * g.RS;
+    RegP Rg = reg_ptr(sm + (long long)r * g.RS, g.RS);
     const int c0 = ctx_of(g, r);
     const unsigned b = it >> logW;
     const int m = (int)(it & (unsigned)(W - 1));

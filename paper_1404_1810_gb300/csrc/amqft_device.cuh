@@ -43,6 +43,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "amqft_debug.cuh"
+
 namespace amqft {
 namespace cg = cooperative_groups;
 
@@ -447,7 +449,7 @@ __device__ __forceinline__ void chain_down_dst(float (&t)[SZ]) {
 }
 
 template <int V, int TH, int TOPM>
-__device__ __forceinline__ void tail_dct(float* R, int half, const SmallConsts& K) {
+__device__ __forceinline__ void tail_dct(RegP R, int half, const SmallConsts& K) {
   constexpr int SZ = TH + 1;
   constexpr int LT = TH / 2;  // size of the top tail tree
   const int base = half - TH;
@@ -492,7 +494,7 @@ __device__ __forceinline__ void tail_dct(float* R, int half, const SmallConsts& 
 }
 
 template <int V, int TH, int TOPM>
-__device__ __forceinline__ void tail_dst(float* R, int half, const SmallConsts& K) {
+__device__ __forceinline__ void tail_dst(RegP R, int half, const SmallConsts& K) {
   if constexpr (TH >= 2) {
     constexpr int SZ = TH - 1;
     constexpr int LT = TH / 2;
@@ -529,7 +531,7 @@ __device__ __forceinline__ void tail_dst(float* R, int half, const SmallConsts& 
 }
 
 template <int V>
-__device__ __noinline__ void run_tail(float* R, int ctx0, int logN, const SmallConsts& K) {
+__device__ __noinline__ void run_tail(RegP R, int ctx0, int logN, const SmallConsts& K) {
   const int half = 1 << (logN - 1);
 #define AMQFT_TAIL(TH, TOPM)                                      \
   if (ctx0 == 0) tail_dct<V, TH, TOPM>(R, half, K);              \
@@ -549,7 +551,7 @@ __device__ __noinline__ void run_tail(float* R, int ctx0, int logN, const SmallC
 // A register subtree of LEAF values: ot trees read time values in natural
 // order and write results bit-reversed; to trees the other way round.
 template <int V>
-__device__ __noinline__ void run_leaf(float* R, int p0, int ctx, const SmallConsts& K) {
+__device__ __noinline__ void run_leaf(RegP R, int p0, int ctx, const SmallConsts& K) {
   float x[LEAF];
   const int f = (p0 >> 5) & 31;  // sw() of a LEAF-aligned row
   if constexpr (Var<V>::ot) {
@@ -626,7 +628,7 @@ __device__ __forceinline__ void pass_neighbour(float* sm, const Geo& g, int logL
     if (w < W) {
       const unsigned r = dv(w), rem = w - r * Wr;
       const int b = (int)(rem >> h), q = (int)(rem & (H - 1)), i = brev(q, h);
-      const float* R = sm + r * g.RS;
+      CRegP R = creg_ptr(sm + r * g.RS, g.RS);
       const int p0 = b << logLp;
       const int ctx = node_ctx_g<V>(g, p0, logLp, ctx_of(g, r));
       const int base = ctx == 0 ? p0 + H : p0;
@@ -655,7 +657,7 @@ __device__ __forceinline__ void pass_neighbour(float* sm, const Geo& g, int logL
     if (w < W) {
       const unsigned r = dv(w), rem = w - r * Wr;
       const int b = (int)(rem >> h), q = (int)(rem & (H - 1));
-      float* R = sm + r * g.RS;
+      RegP R = reg_ptr(sm + r * g.RS, g.RS);
       const int p0 = b << logLp;
       const int ctx = node_ctx_g<V>(g, p0, logLp, ctx_of(g, r));
       const int base = ctx == 0 ? p0 + H : p0;
@@ -726,11 +728,11 @@ __device__ __forceinline__ void pass_recurrence(float* sm, float* tot, float* ws
   float l[MAXI];
   int base = 0, k = 0, kidx = 0;
   bool prefix = true;
-  float* R = sm;
+  RegP R = reg_ptr(sm, g.RS);
   if ((unsigned)tau < nch) {
     const int seg = tau >> logSC, col = tau & (SC - 1);
     const unsigned r = dv((unsigned)seg), b = (unsigned)seg - r * nb;
-    R = sm + r * g.RS;
+    R = reg_ptr(sm + r * g.RS, g.RS);
     const int p0 = (int)(b << logLp);
     const int ctx = node_ctx_g<V>(g, p0, logLp, ctx_of(g, r));
     base = ctx == 0 ? p0 + H : p0;
@@ -789,7 +791,7 @@ __device__ __forceinline__ void pass_chain(float* sm, const Geo& g, int logM) {
     const unsigned w = threadIdx.x + (unsigned)s * TPB;
     if (w < W) {
       const int r = (int)(w >> logQ), k = (int)(w & (Q - 1));
-      const float* R = sm + r * g.RS;
+      CRegP R = creg_ptr(sm + r * g.RS, g.RS);
       const int c = ctx_of(g, r);
       if constexpr (Var<V>::ot) {
         if (c == 0) {
@@ -818,7 +820,7 @@ __device__ __forceinline__ void pass_chain(float* sm, const Geo& g, int logM) {
     const unsigned w = threadIdx.x + (unsigned)s * TPB;
     if (w < W) {
       const int r = (int)(w >> logQ), k = (int)(w & (Q - 1));
-      float* R = sm + r * g.RS;
+      RegP R = reg_ptr(sm + r * g.RS, g.RS);
       const int c = ctx_of(g, r);
       if constexpr (Var<V>::ot) {
         if (c == 0) {

@@ -22,14 +22,14 @@ struct Regions {
   float* sm;
   int RS;
   long long tbase;
-  __device__ __forceinline__ float* get(int tau, int kind) const {
+  __device__ __forceinline__ RegP get(int tau, int kind) const {
     if constexpr (CL == 1) {
-      return sm + (4 * tau + kind) * RS;
+      return reg_ptr(sm + (4 * tau + kind) * RS, RS);
     } else {
       constexpr int PER = 4 / CL;
       cg::cluster_group cl = cg::this_cluster();
       float* remote = cl.map_shared_rank(sm, kind / PER);
-      return remote + (kind % PER) * RS;
+      return reg_ptr(remote + (kind % PER) * RS, RS);
     }
   }
 };
@@ -37,7 +37,7 @@ struct Regions {
 // ---- HBM elements: complex64, or 16-bit complex (a bf16 or fp16 pair, real
 // part in the low half) holding value * 2^-exp with one exponent per
 // transform ----
-constexpr int DT_C64 = 0, DT_BF16 = 1, DT_F16 = 2;  // amqft_dtype
+constexpr int DT_C64 = 0, DT_BF16 = 1, DT_F16 = 2, DT_I16 = 3;  // amqft_dtype
 
 struct InRef {
   const void* p;
@@ -53,11 +53,20 @@ __device__ __forceinline__ float pow2f(int e) {
 
 __device__ __forceinline__ float2 unpack16(unsigned u, int dtype) {
   if (dtype == DT_BF16) return make_float2(__uint_as_float(u << 16), __uint_as_float(u & 0xffff0000u));
+  if (dtype == DT_I16) return make_float2((float)(short)(u & 0xffffu), (float)(short)(u >> 16));
   return make_float2(__half2float(__ushort_as_half((unsigned short)(u & 0xffffu))),
                      __half2float(__ushort_as_half((unsigned short)(u >> 16))));
 }
 
+// int16: round to nearest even, saturated (a scaled output stays below 2^14)
+__device__ __forceinline__ unsigned pack_i16(float v) {
+  int q = __float2int_rn(v);
+  q = q < -32768 ? -32768 : (q > 32767 ? 32767 : q);
+  return (unsigned)(unsigned short)(short)q;
+}
+
 __device__ __forceinline__ unsigned pack16(float re, float im, int dtype) {
+  if (dtype == DT_I16) return pack_i16(re) | (pack_i16(im) << 16);
   if (dtype == DT_BF16)
     return (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(re)) |
            ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(im)) << 16);
@@ -106,7 +115,10 @@ __device__ __forceinline__ Fetched load_fetch(const InRef& in, int logN, long lo
   const unsigned* __restrict__ z16 = static_cast<const unsigned*>(in.p) + off;
   const bool c64 = in.dtype == DT_C64;  // the same for every thread
   const float s = (!c64 && in.exp) ? pow2f(__ldg(in.exp + t)) : 1.f;
-  auto ld = [&](int i) { return c64 ? ldz(z, i, cj) : ldz16(z16, i, in.dtype, s, cj); };
+  auto ld = [&](int i) {
+    if (!AMQFT_IN_BOUNDS(i, N, BS_HBM_IN)) return make_float2(0.f, 0.f);
+    return c64 ? ldz(z, i, cj) : ldz16(z16, i, in.dtype, s, cj);
+  };
   Fetched f;
   if (n == 0) {
     f.a = ld(0);
@@ -235,10 +247,10 @@ __device__ __forceinline__ DrItem load_fetch_trig(const float* __restrict__ dct,
 template <int V, class RG>
 __device__ __forceinline__ void load_place(const RG& rg, int logN, int tau, int n, const DrItem& r) {
   const int N = 1 << logN, half = N >> 1, Q = N >> 2, logQ = logN - 2;
-  float* C1 = rg.get(tau, 0);
-  float* S1 = rg.get(tau, 1);
-  float* C2 = rg.get(tau, 2);
-  float* S2 = rg.get(tau, 3);
+  RegP C1 = rg.get(tau, 0);
+  RegP S1 = rg.get(tau, 1);
+  RegP C2 = rg.get(tau, 2);
+  RegP S2 = rg.get(tau, 3);
   if (n == 0) {
     if (N == 2) {
       C1[0] = r.a1; C1[1] = r.b1; C2[0] = r.a2; C2[1] = r.b2;
@@ -290,10 +302,10 @@ struct Gathered {
 template <int V, class RG>
 __device__ __forceinline__ Gathered store_gather(const RG& rg, int logN, int tau, int k) {
   const int N = 1 << logN, half = N >> 1, Q = N >> 2, logQ = logN - 2;
-  const float* C1 = rg.get(tau, 0);
-  const float* S1 = rg.get(tau, 1);
-  const float* C2 = rg.get(tau, 2);
-  const float* S2 = rg.get(tau, 3);
+  CRegP C1 = rg.get(tau, 0);
+  CRegP S1 = rg.get(tau, 1);
+  CRegP C2 = rg.get(tau, 2);
+  CRegP S2 = rg.get(tau, 3);
   Gathered g;
   if (k == 0) {
     if (N == 2) {
@@ -442,9 +454,10 @@ __device__ __forceinline__ void store_emit(float2* __restrict__ out, int logN, l
                                            float cj) {
   const Out4 o = emit_values<V>(logN, k, g);
   float2* __restrict__ z = out + off;
+  const int N = 1 << logN;
 #pragma unroll
   for (int j = 0; j < 4; ++j)
-    if (o.i[j] >= 0) stz(z, o.i[j], o.v[j].x, o.v[j].y, cj);
+    if (o.i[j] >= 0 && AMQFT_IN_BOUNDS(o.i[j], N, BS_HBM_OUT)) stz(z, o.i[j], o.v[j].x, o.v[j].y, cj);
 }
 
 // 16-bit output of one item, every value times s = 2^-exp (exact)
@@ -468,7 +481,7 @@ __device__ __forceinline__ void store16(unsigned* __restrict__ out, long long of
 // result is written in natural order, unswizzled, word k holding harmonic k
 // (DST words 0 and N/2 zero), the layout the cluster store reads.
 template <int V, int TPB, int LOGM, bool FINAL>
-__device__ __forceinline__ void pass_chain2(float* R, int half, int ctx) {
+__device__ __forceinline__ void pass_chain2(RegP R, int half, int ctx) {
   constexpr int M = 1 << LOGM, Q1 = M / 4, Q2 = M / 2, L1 = LOGM - 2, L2 = LOGM - 1;
   constexpr int NI = (Q1 + 1 + TPB - 1) / TPB;
   const int P1 = half - M / 2, P2 = half - M;
@@ -560,7 +573,7 @@ __device__ __forceinline__ void pass_chain2(float* R, int half, int ctx) {
 
 // Pairs of chain levels LO, LO + 1, ... below the final pair (LN - 1, LN).
 template <int V, int TPB, int LN, int LO>
-__device__ __forceinline__ void chain_pairs(float* R, int half, int ctx) {
+__device__ __forceinline__ void chain_pairs(RegP R, int half, int ctx) {
   if constexpr (LO + 1 <= LN - 2) {
     pass_chain2<V, TPB, LO, false>(R, half, ctx);
     __syncthreads();
@@ -580,7 +593,7 @@ __device__ __forceinline__ void chain_pairs(float* R, int half, int ctx) {
 // S(Q) = O(Q-1).  Harmonics-first variants only undo the chain layout.
 // Every thread reads its values, then the block synchronises, then writes.
 template <int V, int TPB, int LN>
-__device__ __forceinline__ void region_to_natural(float* R, int ctx) {
+__device__ __forceinline__ void region_to_natural(RegP R, int ctx) {
   constexpr int N = 1 << LN, half = N >> 1, Q = N >> 2, logQ = LN - 2;
   if constexpr (Var<V>::ot) {
     constexpr int NI = Q / TPB;
@@ -877,10 +890,10 @@ __device__ __forceinline__ void fused_compute(float* sm, const Geo& g, const Tab
         if (w < g.nreg * nleaf) {
           const int r = (int)dv((unsigned)w), b = w - r * nleaf;
           const int p0 = b << LOG_LEAF;
-          run_leaf<V>(sm + r * g.RS, p0, node_ctx_g<V>(g, p0, LOG_LEAF, ctx_of(g, r)), K);
+          run_leaf<V>(reg_ptr(sm + r * g.RS, g.RS), p0, node_ctx_g<V>(g, p0, LOG_LEAF, ctx_of(g, r)), K);
         } else {
           const int r = w - g.nreg * nleaf;
-          run_tail<V>(sm + r * g.RS, ctx_of(g, r), logN, K);
+          run_tail<V>(reg_ptr(sm + r * g.RS, g.RS), ctx_of(g, r), logN, K);
         }
       }
       __syncthreads();
@@ -907,8 +920,8 @@ __device__ __forceinline__ void fused_compute(float* sm, const Geo& g, const Tab
         pass_chain<V, TPB, MAXI>(sm, g, LO);
         __syncthreads();
       }
-      chain_pairs<V, TPB, LN, LO2>(sm, half, ctx);
-      pass_chain2<V, TPB, LN - 1, true>(sm, half, ctx);
+      chain_pairs<V, TPB, LN, LO2>(reg_ptr(sm, region_stride(LN)), half, ctx);
+      pass_chain2<V, TPB, LN - 1, true>(reg_ptr(sm, region_stride(LN)), half, ctx);
     } else {
       for (int lm = LOG_LEAF + 2; lm <= logN - 1; ++lm) {
         pass_chain<V, TPB, MAXI>(sm, g, lm);
@@ -920,7 +933,7 @@ __device__ __forceinline__ void fused_compute(float* sm, const Geo& g, const Tab
       pass_chain<V, TPB, MAXI>(sm, g, lm);
       __syncthreads();
     }
-    for (int r = threadIdx.x; r < g.nreg; r += TPB) run_tail<V>(sm + r * g.RS, ctx_of(g, r), logN, K);
+    for (int r = threadIdx.x; r < g.nreg; r += TPB) run_tail<V>(reg_ptr(sm + r * g.RS, g.RS), ctx_of(g, r), logN, K);
     __syncthreads();
     for (int lp = logTop; lp >= LOG_LEAF + 1; --lp) {
       if constexpr (Var<V>::scan) pass_recurrence<V, TPB, MAXI>(sm, tot, wsum, g, lp);
@@ -934,7 +947,7 @@ __device__ __forceinline__ void fused_compute(float* sm, const Geo& g, const Tab
       for (int w = threadIdx.x; w < W; w += TPB) {
         const int r = (int)dv((unsigned)w), b = w - r * nleaf;
         const int p0 = b << LOG_LEAF;
-        run_leaf<V>(sm + r * g.RS, p0, node_ctx_g<V>(g, p0, LOG_LEAF, ctx_of(g, r)), K);
+        run_leaf<V>(reg_ptr(sm + r * g.RS, g.RS), p0, node_ctx_g<V>(g, p0, LOG_LEAF, ctx_of(g, r)), K);
       }
       __syncthreads();
     }
@@ -1003,41 +1016,56 @@ __device__ __forceinline__ void fused_body(const FusedArgs& a, const SmallConsts
   constexpr int NIT = (CL > 1 && LN > 0) ? (1 << (LN - 4)) / TPB : 2048 / TPB;
   constexpr int U = NIT < 4 ? NIT : 4, NR = NIT / U;
   static_assert(NR * U == NIT, "orbit items per thread");
+  // item idx of this thread for the load: (local transform, orbit item n)
+  auto load_item = [&](int idx, int& tau, int& n) -> bool {
+    if constexpr (CL == 1) {
+      const int w = threadIdx.x + idx * TPB;
+      tau = w >> logQi;
+      n = w & (Qi - 1);
+      return tau < ntr;
+    } else {
+      const int per = Qi / CL;
+      tau = 0;
+      n = (int)cg::this_cluster().block_rank() * per + threadIdx.x + idx * TPB;
+      return (int)threadIdx.x + idx * TPB < per;
+    }
+  };
+  if (a.ntrig > 0) {
+    // DCT-0 / DST-0 inputs straight into the regions
 #pragma unroll 1
-  for (int rd = 0; rd < NR; ++rd) {
-    int n_[U], tau_[U];
-    bool ok_[U];
-    DrItem r_[U];
+    for (int rd = 0; rd < NR; ++rd) {
+      int n_[U], tau_[U];
+      bool ok_[U];
+      DrItem r_[U];
 #pragma unroll
-    for (int s = 0; s < U; ++s) {
-      const int idx = rd * U + s;
-      if constexpr (CL == 1) {
-        const int w = threadIdx.x + idx * TPB;
-        tau_[s] = w >> logQi;
-        n_[s] = w & (Qi - 1);
-        ok_[s] = tau_[s] < ntr;
-      } else {
-        const int per = Qi / CL;
-        tau_[s] = 0;
-        n_[s] = (int)cg::this_cluster().block_rank() * per + threadIdx.x + idx * TPB;
-        ok_[s] = (int)threadIdx.x + idx * TPB < per;
+      for (int s = 0; s < U; ++s) {
+        ok_[s] = load_item(rd * U + s, tau_[s], n_[s]);
+        if (ok_[s]) r_[s] = load_fetch_trig(static_cast<const float*>(a.in), a.in2, a.ntrig, logN, tid(tau_[s]), n_[s]);
       }
-      if (ok_[s]) {
-        const long long t = tid(tau_[s]);
-        if (a.ntrig > 0) {
-          r_[s] = load_fetch_trig(static_cast<const float*>(a.in), a.in2, a.ntrig, logN, t, n_[s]);
-        } else {
-          const Fetched f =
-              a.nreal > 0 ? load_fetch_real(static_cast<const float*>(a.in), logN, t, a.nreal, n_[s])
-              : a.nirdft > 0 ? load_fetch_irdft(static_cast<const float2*>(a.in), logN, t, a.nirdft, n_[s])
-                             : load_fetch(InRef{a.in, a.exp_in, a.dtype}, logN, t, toff(t), n_[s], cj);
-          r_[s] = d_r(f, N, n_[s]);
+#pragma unroll
+      for (int s = 0; s < U; ++s)
+        if (ok_[s]) load_place<V>(rg, logN, tau_[s], n_[s], r_[s]);
+    }
+  } else {
+#pragma unroll 1
+    for (int rd = 0; rd < NR; ++rd) {
+      int n_[U], tau_[U];
+      bool ok_[U];
+      Fetched f_[U];
+#pragma unroll
+      for (int s = 0; s < U; ++s) {
+        ok_[s] = load_item(rd * U + s, tau_[s], n_[s]);
+        if (ok_[s]) {
+          const long long t = tid(tau_[s]);
+          f_[s] = a.nreal > 0 ? load_fetch_real(static_cast<const float*>(a.in), logN, t, a.nreal, n_[s])
+                  : a.nirdft > 0 ? load_fetch_irdft(static_cast<const float2*>(a.in), logN, t, a.nirdft, n_[s])
+                                 : load_fetch(InRef{a.in, a.exp_in, a.dtype}, logN, t, toff(t), n_[s], cj);
         }
       }
-    }
 #pragma unroll
-    for (int s = 0; s < U; ++s)
-      if (ok_[s]) load_place<V>(rg, logN, tau_[s], n_[s], r_[s]);
+      for (int s = 0; s < U; ++s)
+        if (ok_[s]) load_scatter<V>(rg, logN, tau_[s], n_[s], f_[s]);
+    }
   }
   if constexpr (CL == 1) __syncthreads();
   else cg::this_cluster().sync();
@@ -1051,7 +1079,7 @@ __device__ __forceinline__ void fused_body(const FusedArgs& a, const SmallConsts
     // time-first variants: the final chain pair already wrote natural order
     if constexpr (!Var<V>::ot) {
       __syncthreads();
-      region_to_natural<V, TPB, LN>(sm, (int)cg::this_cluster().block_rank() & 1);
+      region_to_natural<V, TPB, LN>(reg_ptr(sm, region_stride(LN)), (int)cg::this_cluster().block_rank() & 1);
     }
     cg::this_cluster().sync();
     const long long t = tid(0);
@@ -1180,6 +1208,16 @@ template <int V>
 cudaError_t launch_v(const FusedArgs& a, const SmallConsts& K, const FusedConfig& c, cudaStream_t st) {
   if (c.cluster == 1) {
     const long long grid = (a.batch + c.per_cta - 1) / c.per_cta;
+    // A call that fills one CTA at most is latency-bound: 512 threads (half
+    // the items per thread in every pass), one CTA per SM.  Only for the
+    // variants without recurrences, whose results do not depend on the
+    // thread count (the recurrences' scan chunking does), so a transform's
+    // bits never depend on its batch.
+    if constexpr (!Var<V>::scan) {
+      if (grid == 1)
+        return launch_cfg<V, 2 * SMALL_TPB, SMALL_MAXI / 2, 1, 0>(a, K, grid, c.smem + SMALL_TPB * (int)sizeof(float),
+                                                                  st);
+    }
     return launch_cfg<V, SMALL_TPB, SMALL_MAXI, 1, 0>(a, K, grid, c.smem, st);
   }
   switch (a.logN) {

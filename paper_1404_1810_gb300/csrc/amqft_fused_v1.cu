@@ -14,4 +14,5 @@ cudaError_t ragged_variant_1(const FusedArgs& a, const SmallConsts& K, const Rag
                                cudaStream_t st, long long* nlaunch) {
   return ragged_run<1>(a, K, r, L, st, nlaunch);
 }
+AMQFT_BOUNDS_READER(bounds_v1)
 }  // namespace amqft

@@ -14,4 +14,5 @@ cudaError_t ragged_variant_2(const FusedArgs& a, const SmallConsts& K, const Rag
                                cudaStream_t st, long long* nlaunch) {
   return ragged_run<2>(a, K, r, L, st, nlaunch);
 }
+AMQFT_BOUNDS_READER(bounds_v2)
 }  // namespace amqft

@@ -68,6 +68,22 @@ cudaError_t multipass_variant_8(const MpArgs&, float*, float*, const SmallConsts
 cudaError_t multipass_dispatch(int variant, const MpArgs& a, float* W0, float* W1, const SmallConsts& K,
                                cudaStream_t st, long long* nlaunch);
 
+// bounds-checked build: each translation unit's failure count and first
+// failure (amqft_debug.cuh), read and optionally cleared
+#define AMQFT_BOUNDS_DECL(name) cudaError_t name(unsigned long long* count, unsigned long long* first, bool clear);
+AMQFT_BOUNDS_DECL(bounds_v1)
+AMQFT_BOUNDS_DECL(bounds_v2)
+AMQFT_BOUNDS_DECL(bounds_v3)
+AMQFT_BOUNDS_DECL(bounds_v4)
+AMQFT_BOUNDS_DECL(bounds_v5)
+AMQFT_BOUNDS_DECL(bounds_v6)
+AMQFT_BOUNDS_DECL(bounds_v7)
+AMQFT_BOUNDS_DECL(bounds_v8)
+AMQFT_BOUNDS_DECL(bounds_p14)
+AMQFT_BOUNDS_DECL(bounds_p15)
+AMQFT_BOUNDS_DECL(bounds_p16)
+#undef AMQFT_BOUNDS_DECL
+
 // paired-region kernel (N = 2^14 .. 2^16, variant 4, complex64, batch below
 // 2^31): one transform per cluster of four CTAs, persistent over the batch;
 // in and out 16-byte aligned

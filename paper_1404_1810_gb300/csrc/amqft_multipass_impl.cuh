@@ -71,7 +71,9 @@ __device__ __forceinline__ long long mp_off(const MpArgs& a, long long id) {
 struct GRegions {
   float* W;
   long long RSg;
-  __device__ __forceinline__ float* get(long long t, int kind) const { return W + (t * 4 + kind) * RSg; }
+  __device__ __forceinline__ RegP get(long long t, int kind) const {
+    return reg_ptr(W + (t * 4 + kind) * RSg, (int)RSg);
+  }
 };
 
 template <int V>
@@ -194,7 +196,7 @@ __global__ void mp_neighbour_kernel(MpArgs a, const float* __restrict__ Win, flo
     const long long rr = w / a.RSg;
     const int ph = (int)(w - rr * a.RSg);  // physical (swizzled) word
     const int p = sw(ph);                  // logical position (sw is an involution)
-    const float* R = Win + rr * a.RSg;
+    CRegP R = creg_ptr(Win + rr * a.RSg, (int)a.RSg);
     float v = R[ph];
     if (p < half - Lp) {
       const int p0 = p & ~(Lp - 1), qn = p - p0;
@@ -245,7 +247,7 @@ __device__ __forceinline__ bool rec_prefix(int ctx) {
 }
 
 struct RecChunk {
-  float* R;      // the region
+  RegP R;       // the region
   long long nd;  // node index over the chunk's regions
   int base;      // first position of the node's B half
   int col, k, logSC;
@@ -272,7 +274,7 @@ __device__ __forceinline__ RecChunk rec_chunk(const MpArgs& a, float* W, int log
   const long long rr = c.nd / nb;
   const int p0 = (int)(c.nd - rr * nb) << logLp;
   const int ctx = node_ctx<V>(p0, logLp, half, (int)(rr & 1));
-  c.R = W + rr * a.RSg;
+  c.R = reg_ptr(W + rr * a.RSg, (int)a.RSg);
   c.base = ctx == 0 ? p0 + H : p0;
   c.prefix = rec_prefix<V>(ctx);
   const int bc = brev(c.col, c.logSC);
@@ -377,7 +379,7 @@ __global__ void mp_chain_kernel(MpArgs a, const float* __restrict__ Win, float* 
     const long long rr = w / a.RSg;
     const int ph = (int)(w - rr * a.RSg);
     const int p = sw(ph);
-    const float* R = Win + rr * a.RSg;
+    CRegP R = creg_ptr(Win + rr * a.RSg, (int)a.RSg);
     const int ctx0 = (int)(rr & 1);
     float v = R[ph];
     const int rel = p - P;
@@ -436,7 +438,7 @@ __global__ void __launch_bounds__(TPB) mp_solve_kernel(MpArgs a, float* W, const
   const long long rr = blockIdx.x / per;
   if (rr >= 4 * mp_nt(a)) return;  // launched for the capacity (uniform per block, before any barrier)
   const int sidx = (int)(blockIdx.x - rr * per);
-  float* R = W + rr * a.RSg;
+  RegP R = reg_ptr(W + rr * a.RSg, (int)a.RSg);
   const int ctx0 = (int)(rr & 1);
   const int RSn = MP_S + 32;
   float* tot = sm + 2 * RSn + 64;  // scratch after the largest layout (tail: 2S + 32 words)
@@ -475,7 +477,7 @@ __global__ void __launch_bounds__(TPB) mp_solve_kernel(MpArgs a, float* W, const
       }
       for (int w = threadIdx.x; w < 2 * nleaf; w += TPB) {
         const int r = w / nleaf, p0 = (w - r * nleaf) << LOG_LEAF;
-        run_leaf<V>(sm + r * RSn, p0, node_ctx_g<V>(g, p0, LOG_LEAF, ctx_of(g, r)), K);
+        run_leaf<V>(reg_ptr(sm + r * RSn, RSn), p0, node_ctx_g<V>(g, p0, LOG_LEAF, ctx_of(g, r)), K);
       }
       __syncthreads();
       if constexpr (Var<V>::scan) {
@@ -497,7 +499,7 @@ __global__ void __launch_bounds__(TPB) mp_solve_kernel(MpArgs a, float* W, const
       }
       for (int w = threadIdx.x; w < 2 * nleaf; w += TPB) {
         const int r = w / nleaf, p0 = (w - r * nleaf) << LOG_LEAF;
-        run_leaf<V>(sm + r * RSn, p0, node_ctx_g<V>(g, p0, LOG_LEAF, ctx_of(g, r)), K);
+        run_leaf<V>(reg_ptr(sm + r * RSn, RSn), p0, node_ctx_g<V>(g, p0, LOG_LEAF, ctx_of(g, r)), K);
       }
       __syncthreads();
       for (int b = bp.nb - 1; b >= 0; --b) {
@@ -531,8 +533,8 @@ __global__ void __launch_bounds__(TPB) mp_solve_kernel(MpArgs a, float* W, const
         __syncthreads();
       }
       for (int w = threadIdx.x; w < nleaf + 1; w += TPB) {
-        if (w < nleaf) run_leaf<V>(sm, w << LOG_LEAF, node_ctx_g<V>(g, w << LOG_LEAF, LOG_LEAF, ctx0), K);
-        else run_tail<V>(sm, ctx0, logNp, K);
+        if (w < nleaf) run_leaf<V>(reg_ptr(sm, g.RS), w << LOG_LEAF, node_ctx_g<V>(g, w << LOG_LEAF, LOG_LEAF, ctx0), K);
+        else run_tail<V>(reg_ptr(sm, g.RS), ctx0, logNp, K);
       }
       __syncthreads();
       if constexpr (Var<V>::scan) {
@@ -555,7 +557,7 @@ __global__ void __launch_bounds__(TPB) mp_solve_kernel(MpArgs a, float* W, const
         pass_chain<V, TPB, 32>(sm, g, lm);
         __syncthreads();
       }
-      if (threadIdx.x == 0) run_tail<V>(sm, ctx0, logNp, K);
+      if (threadIdx.x == 0) run_tail<V>(reg_ptr(sm, g.RS), ctx0, logNp, K);
       __syncthreads();
       for (int lp = logNp - 2; lp >= LOG_LEAF + 1; --lp) {
         if constexpr (Var<V>::scan) pass_recurrence<V, TPB, 16>(sm, tot, wsum, g, lp);
@@ -563,7 +565,7 @@ __global__ void __launch_bounds__(TPB) mp_solve_kernel(MpArgs a, float* W, const
         __syncthreads();
       }
       for (int w = threadIdx.x; w < nleaf; w += TPB)
-        run_leaf<V>(sm, w << LOG_LEAF, node_ctx_g<V>(g, w << LOG_LEAF, LOG_LEAF, ctx0), K);
+        run_leaf<V>(reg_ptr(sm, g.RS), w << LOG_LEAF, node_ctx_g<V>(g, w << LOG_LEAF, LOG_LEAF, ctx0), K);
       __syncthreads();
       for (int b = bp.nb - 1; b >= 0; --b) {
         run_fold_band_r<V, TPB>(sm, g, bp.logL[b], bp.R[b], false, cs);

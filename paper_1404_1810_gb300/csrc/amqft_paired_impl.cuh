@@ -13,6 +13,21 @@ namespace pr {
 struct DevCtx {
   int tid, rank;
   unsigned lbase;  // shared-window address of this CTA's region
+#ifdef AMQFT_BOUNDS_CHECK
+  // bounds of the checked build: region float2 words, and the batch in HBM
+  int rf;
+  const float2* gin;
+  const float2* gout;
+  long long gn;
+  __device__ __forceinline__ bool reg_ok(int i, int w) const { return AMQFT_IN_BOUNDS(i, rf - (w - 1), BS_PAIRED_REG); }
+  __device__ __forceinline__ bool hbm_ok(const float2* p, const float2* base, int w) const {
+    return AMQFT_IN_BOUNDS(p - base, gn - (w - 1), BS_PAIRED_HBM);
+  }
+#define PAIRED_CHECK(cond, fallback) \
+  if (!(cond)) return fallback
+#else
+#define PAIRED_CHECK(cond, fallback)
+#endif
   // shared::cluster address of CTA q's region (mapa, recomputed at each use
   // rather than held in four registers through the whole transform)
   __device__ __forceinline__ unsigned cbase(int q) const {
@@ -23,16 +38,29 @@ struct DevCtx {
   __device__ __forceinline__ void sync_warp() { __syncwarp(); }
   __device__ __forceinline__ void sync_cta() { __syncthreads(); }
   __device__ __forceinline__ void sync_cluster() { cg::this_cluster().sync(); }
-  __device__ __forceinline__ float4 ldg4(const float2* p) { return __ldcs(reinterpret_cast<const float4*>(p)); }
-  __device__ __forceinline__ float2 ldg2(const float2* p) { return __ldcs(p); }
-  __device__ __forceinline__ void stg4(float2* p, float4 v) { __stcs(reinterpret_cast<float4*>(p), v); }
-  __device__ __forceinline__ void stg2(float2* p, float2 v) { __stcs(p, v); }
+  __device__ __forceinline__ float4 ldg4(const float2* p) {
+    PAIRED_CHECK(hbm_ok(p, gin, 2), make_float4(0.f, 0.f, 0.f, 0.f));
+    return __ldcs(reinterpret_cast<const float4*>(p));
+  }
+  __device__ __forceinline__ float2 ldg2(const float2* p) {
+    PAIRED_CHECK(hbm_ok(p, gin, 1), make_float2(0.f, 0.f));
+    return __ldcs(p);
+  }
+  __device__ __forceinline__ void stg4(float2* p, float4 v) {
+    PAIRED_CHECK(hbm_ok(p, gout, 2), );
+    __stcs(reinterpret_cast<float4*>(p), v);
+  }
+  __device__ __forceinline__ void stg2(float2* p, float2 v) {
+    PAIRED_CHECK(hbm_ok(p, gout, 1), );
+    __stcs(p, v);
+  }
   __device__ __forceinline__ float2 shfl_up(float2 v, int d) {
     return make_float2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
   }
   // float2 index i of CTA q's region: the own region through the shared
   // window, the others as distributed shared memory, 32-bit addresses
   __device__ __forceinline__ void dst2(int q, int i, float2 v) {
+    PAIRED_CHECK(reg_ok(i, 1), );
     if (q == rank)
       asm volatile("st.shared.v2.f32 [%0], {%1, %2};" ::"r"(lbase + 8u * (unsigned)i), "f"(v.x), "f"(v.y) : "memory");
     else
@@ -40,6 +68,7 @@ struct DevCtx {
                    : "memory");
   }
   __device__ __forceinline__ float2 dld2(int q, int i) {
+    PAIRED_CHECK(reg_ok(i, 1), make_float2(0.f, 0.f));
     float2 v;
     if (q == rank)
       asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(lbase + 8u * (unsigned)i) : "memory");
@@ -50,6 +79,12 @@ struct DevCtx {
   }
   // two float2 at index i (even): one 16-byte access
   __device__ __forceinline__ void dld4(int q, int i, float2* v) {
+#ifdef AMQFT_BOUNDS_CHECK
+    if (!reg_ok(i, 2)) {
+      v[0] = v[1] = make_float2(0.f, 0.f);
+      return;
+    }
+#endif
     float a, b, c, d;
     if (q == rank)
       asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];" : "=f"(a), "=f"(b), "=f"(c), "=f"(d)
@@ -77,6 +112,12 @@ __global__ void __launch_bounds__(paired_tpb(LN), paired_ctas(LN))
   cx.tid = (int)threadIdx.x;
   cx.rank = (int)cl.block_rank();
   cx.lbase = (unsigned)__cvta_generic_to_shared(psm);
+#ifdef AMQFT_BOUNDS_CHECK
+  cx.rf = region_f2<T>();
+  cx.gin = in;
+  cx.gout = out;
+  cx.gn = batch << LN;
+#endif
   float* cst = reinterpret_cast<float*>(psm + region_f2<T>());
   if (!ctab) {  // constants on the fly: the same entries paired_body copies from the table
     const int ncst = (cx.rank & 1) == 0 ? (1 << T) - 32 : (1 << (T - 1)) - 32;

@@ -6,4 +6,5 @@ cudaError_t paired_launch_14(const void* in, void* out, long long batch, int inv
                                const SmallConsts& K, cudaStream_t st) {
   return pr::launch_len<14>(in, out, batch, inverse, ctab, K, st);
 }
+AMQFT_BOUNDS_READER(bounds_p14)
 }  // namespace amqft

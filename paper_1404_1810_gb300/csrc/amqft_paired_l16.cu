@@ -6,4 +6,5 @@ cudaError_t paired_launch_16(const void* in, void* out, long long batch, int inv
                                const SmallConsts& K, cudaStream_t st) {
   return pr::launch_len<16>(in, out, batch, inverse, ctab, K, st);
 }
+AMQFT_BOUNDS_READER(bounds_p16)
 }  // namespace amqft

@@ -1,5 +1,6 @@
-"""16-bit storage (bf16 / fp16 pairs with one power-of-two exponent per
-transform, float32 arithmetic) against the oracle.
+"""16-bit storage (bf16 / fp16 / int16 pairs with one power-of-two exponent
+per transform, float32 arithmetic; int16 is the block-floating-point form)
+against the oracle.
 
 Variants 2, 4, 6, 8 compute the same float32 values as the oracle's float32
 recursion, so their 16-bit output is pinned bit for bit: the exponent from
@@ -16,7 +17,8 @@ from gpu_util import expected_exponent, rel
 
 pytestmark = pytest.mark.gpu
 
-AMQFT_CBF16, AMQFT_CF16 = 1, 2
+AMQFT_CBF16, AMQFT_CF16, AMQFT_CI16 = 1, 2, 3
+DTYPES = [AMQFT_CBF16, AMQFT_CF16, AMQFT_CI16]
 
 
 @pytest.fixture(scope="module", autouse=True)
@@ -33,14 +35,22 @@ def lib():
 def _tdt(dt):
     import torch
 
-    return torch.bfloat16 if dt == AMQFT_CBF16 else torch.float16
+    return {AMQFT_CBF16: torch.bfloat16, AMQFT_CF16: torch.float16, AMQFT_CI16: torch.int16}[dt]
+
+
+def _to16(t, dt):
+    """float tensor -> the 16-bit type: round to nearest even (int16: to the
+    nearest integer, ties to even, as the kernels store it)."""
+    return t.round().to(_tdt(dt)) if dt == AMQFT_CI16 else t.to(_tdt(dt))
 
 
 def quantize_input(x, dt):
-    """(b, n) complex128 -> (b, n, 2) 16-bit CPU tensor (round to nearest even)."""
+    """(b, n) complex128 -> (b, n, 2) 16-bit CPU tensor (round to nearest even;
+    int16 holds the signal times 2^12, exponent 0)."""
     import torch
 
-    return torch.view_as_real(torch.from_numpy(np.ascontiguousarray(x))).to(_tdt(dt)).contiguous()
+    t = torch.view_as_real(torch.from_numpy(np.ascontiguousarray(x)))
+    return _to16(t * 4096.0 if dt == AMQFT_CI16 else t, dt).contiguous()
 
 
 def run16(x16, log2n, v, dt, inverse=False, exp_in=None):
@@ -66,7 +76,7 @@ CASES = [(0, 4), (1, 4), (2, 2), (3, 8), (10, 4), (10, 2), (13, 6), (14, 4), (15
          (17, 6)]
 
 
-@pytest.mark.parametrize("dt", [AMQFT_CBF16, AMQFT_CF16])
+@pytest.mark.parametrize("dt", DTYPES)
 @pytest.mark.parametrize("log2n,v", CASES)
 def test_16bit_bit_exact(orc, dt, log2n, v):
     import torch
@@ -82,11 +92,11 @@ def test_16bit_bit_exact(orc, dt, log2n, v):
         ee = expected_exponent(r32)
         assert int(e[i]) == ee, (i, int(e[i]), ee)
         scaled = (r32 * np.float32(2.0 ** -ee)).astype(np.complex64)
-        want = torch.view_as_real(torch.from_numpy(scaled)).to(_tdt(dt))
+        want = _to16(torch.view_as_real(torch.from_numpy(scaled)), dt)
         assert torch.equal(y16[i].view(torch.int16), want.view(torch.int16)), (log2n, v, i)
 
 
-@pytest.mark.parametrize("dt", [AMQFT_CBF16, AMQFT_CF16])
+@pytest.mark.parametrize("dt", DTYPES)
 @pytest.mark.parametrize("family", ["gauss", "multitone"])
 @pytest.mark.parametrize("log2n,v", [(10, 1), (10, 3), (10, 5), (10, 7), (10, 2), (14, 1), (14, 3), (16, 4), (16, 1),
                                      (18, 2)])
@@ -111,7 +121,7 @@ def test_16bit_accuracy(orc, dt, family, log2n, v):
         assert rel(y[i], r64) <= tol, (v, log2n, family, rel(y[i], r64), tol)
 
 
-@pytest.mark.parametrize("dt", [AMQFT_CBF16, AMQFT_CF16])
+@pytest.mark.parametrize("dt", DTYPES)
 @pytest.mark.parametrize("log2n", [6, 14, 17])
 def test_16bit_roundtrip_with_exponents(dt, log2n):
     """inv(fwd(x)) with the forward's exponents as exp_in gives N x."""

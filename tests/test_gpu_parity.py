@@ -261,3 +261,30 @@ def test_host_memory_pipeline(log2n, v, b, chunk):
                 assert torch.equal(yh, ref), (inverse, rep)
     finally:
         p.close()
+
+
+@pytest.mark.parametrize("log2n", [6, 10, 13])
+def test_latency_shape_same_bits(log2n):
+    """A call that fits one CTA runs the 512-thread shape (variants without
+    recurrences); its transforms must equal, bit for bit, the same transforms
+    in a larger batch on the 256-thread shape.  Recurrence variants keep the
+    256-thread shape for every batch."""
+    import torch
+
+    from paper_1404_1810_gb300 import Plan
+
+    n = 1 << log2n
+    per = (512 * 32) // (2 * n)            # transforms per CTA of the single-CTA path
+    x = synth.device_normal_complex64(n, per + 1, "cuda", seed_offset=log2n)
+    for v in VARIANTS:
+        small, big = Plan(log2n, v, 1), Plan(log2n, v, per + 1)
+        try:
+            for inverse in (False, True):
+                y1 = small.inv(x[:1].contiguous()) if inverse else small.fwd(x[:1].contiguous())
+                yb = big.inv(x) if inverse else big.fwd(x)
+                torch.cuda.synchronize()
+                bits = lambda t: torch.view_as_real(t).view(torch.int32)  # noqa: E731
+                assert torch.equal(bits(y1[0]), bits(yb[0])), (log2n, v, inverse)
+        finally:
+            small.close()
+            big.close()

@@ -118,8 +118,8 @@ def test_static_rejects_what_it_cannot_hold(lib):
             amqft_exec_static(h, -1, x.data_ptr(), y.data_ptr())
         assert e.value.code == -8
         amqft_exec_static(h, 0, 0, 0)          # empty batch: nothing to do
-        with pytest.raises(AmqftError) as e:   # in and out overlap
-            amqft_exec_static(h, 1, x.data_ptr(), x.data_ptr())
+        with pytest.raises(AmqftError) as e:   # in and out overlap without being equal
+            amqft_exec_static(h, 1, x.data_ptr(), x.data_ptr() + 8 * 64)
         assert e.value.code == -5
     finally:
         amqft_destroy(h)

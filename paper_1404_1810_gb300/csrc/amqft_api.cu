@@ -457,8 +457,8 @@ static int exec_n(amqft_plan_t p, long long batch, const void* in, void* out, in
     ++p->launches;
     return AMQFT_OK;
   }
-  if (paired_supported(p->log2n, p->variant, p->dtype, batch) && !((a0 | b0) & 15u)) {
-    e = paired_launch(p->log2n, in, out, batch, inverse, kernel_ctab(p), p->small, st);
+  if (paired_supported(p->log2n, p->variant, p->dtype, batch) && !((a0 | b0) & (c64 ? 15u : 7u))) {
+    e = paired_launch(p->log2n, in, out, exp_in, exp_out, p->dtype, batch, inverse, kernel_ctab(p), p->small, st);
     if (e != cudaSuccess) return cuda_fail(e, "paired kernel launch");
     ++p->launches;
     return AMQFT_OK;

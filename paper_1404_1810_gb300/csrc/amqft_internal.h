@@ -84,15 +84,18 @@ AMQFT_BOUNDS_DECL(bounds_p15)
 AMQFT_BOUNDS_DECL(bounds_p16)
 #undef AMQFT_BOUNDS_DECL
 
-// paired-region kernel (N = 2^14 .. 2^16, variant 4, complex64, batch below
-// 2^31): one transform per cluster of four CTAs, persistent over the batch;
-// in and out 16-byte aligned
+// paired-region kernel (N = 2^14 .. 2^16, variant 4, complex64 or 16-bit
+// storage, batch below 2^31): one transform per cluster of four CTAs,
+// persistent over the batch; in and out 16-byte (16-bit: 8-byte) aligned
 bool paired_supported(int logN, int variant, int dtype, long long batch);
-cudaError_t paired_launch(int logN, const void* in, void* out, long long batch, int inverse, const float* ctab,
-                          const SmallConsts& K, cudaStream_t st);
-cudaError_t paired_launch_14(const void*, void*, long long, int, const float*, const SmallConsts&, cudaStream_t);
-cudaError_t paired_launch_15(const void*, void*, long long, int, const float*, const SmallConsts&, cudaStream_t);
-cudaError_t paired_launch_16(const void*, void*, long long, int, const float*, const SmallConsts&, cudaStream_t);
+cudaError_t paired_launch(int logN, const void* in, void* out, const int* exp_in, int* exp_out, int dtype,
+                          long long batch, int inverse, const float* ctab, const SmallConsts& K, cudaStream_t st);
+cudaError_t paired_launch_14(const void*, void*, const int*, int*, int, long long, int, const float*, const SmallConsts&,
+                             cudaStream_t);
+cudaError_t paired_launch_15(const void*, void*, const int*, int*, int, long long, int, const float*, const SmallConsts&,
+                             cudaStream_t);
+cudaError_t paired_launch_16(const void*, void*, const int*, int*, int, long long, int, const float*, const SmallConsts&,
+                             cudaStream_t);
 
 // Read-only view of a plan, for entry points defined outside the plan's
 // translation unit.  Returns AMQFT_ERR_ARG for a NULL plan.

@@ -54,6 +54,7 @@
 #pragma once
 
 #include <stdint.h>
+#include <string.h>
 
 #if defined(__CUDACC__)
 #include <cooperative_groups.h>
@@ -747,34 +748,112 @@ PR_HD int rest_pos(int n) {
 // (load_fetch) and scattered into the four regions afterwards (load_scatter),
 // and the first round of the next transform is in flight across the cluster
 // barrier that ends the current one.
-template <int LN>
-struct LoadRound {
-  static constexpr int NT = 1 << (LN - 7), NI = (1 << (LN - 4)) / NT / 4;  // items per round
-  float4 a[NI];
-  float2 m0[NI], m1[NI];
+// The HBM form of the batch: complex64 (H = false) or 16-bit pairs (H =
+// true: bfloat16, binary16 or int16, real part in the low half, the values
+// times 2^exp, one exponent per transform; the Ctx converts, the arithmetic
+// stays float32 and the scalings are exact powers of two).
+struct Store16 {
+  const int* exp_in;  // input exponents (NULL: all 0)
+  int* exp_out;       // output exponents
+  int dtype;          // 1 bf16, 2 fp16, 3 int16
 };
 
-template <int LN, class Ctx>
-PR_HD void load_fetch(Ctx& cx, const float2* __restrict__ xin, int r, int round, LoadRound<LN>& R) {
-  constexpr int N = 1 << LN, NT = LoadRound<LN>::NT, NI = LoadRound<LN>::NI;
+PR_HD float f32_from_bits(uint32_t u) {
+#if defined(__CUDA_ARCH__)
+  return __uint_as_float(u);
+#else
+  float f;
+  memcpy(&f, &u, 4);
+  return f;
+#endif
+}
+
+// 2^e, exact (e clamped to the normal range)
+PR_HD float pow2_exact(int e) {
+  e = e < -126 ? -126 : (e > 127 ? 127 : e);
+  return f32_from_bits((uint32_t)(127 + e) << 23);
+}
+
+// exponent of a 16-bit output transform: its largest component magnitude m
+// lands in [2^13, 2^14) once scaled by 2^-e; 0 for m = 0 or not finite;
+// clamped to [-100, 100]
+PR_HD int block_exp(float m) {
+  if (!(m > 0.f) || !(m <= 3.402823466e38f)) return 0;
+  uint32_t u;
+#if defined(__CUDA_ARCH__)
+  u = __float_as_uint(m);
+#else
+  memcpy(&u, &m, 4);
+#endif
+  int e = (int)((u >> 23) & 0xff) - 127;  // floor(log2 m) for normal m
+  if (e < -126) e = -126;
+  e -= 13;
+  return e < -100 ? -100 : (e > 100 ? 100 : e);
+}
+
+template <bool H>
+struct LoadWords {  // one item: x(n), x(n+1) and x(N-n), x(N-n-1)
+  float4 a;
+  float2 m0, m1;
+};
+template <>
+struct LoadWords<true> {
+  uint2 a;
+  unsigned m0, m1;
+};
+
+template <int LN, bool H = false>
+struct LoadRound {
+  static constexpr int NT = 1 << (LN - 7), NI = (1 << (LN - 4)) / NT / 4;  // items per round
+  LoadWords<H> w[NI];
+};
+
+template <int LN, bool H, class Ctx>
+PR_HD void load_fetch(Ctx& cx, const void* xin, int r, int round, LoadRound<LN, H>& R) {
+  constexpr int N = 1 << LN, NT = LoadRound<LN, H>::NT, NI = LoadRound<LN, H>::NI;
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
     const int n = r * (N / 8) + 2 * (cx.tid + (round * NI + i) * NT);
-    R.a[i] = cx.ldg4(xin + n);
-    R.m0[i] = n > 0 ? cx.ldg2(xin + (N - n)) : make_float2(0.f, 0.f);
-    R.m1[i] = cx.ldg2(xin + (N - n - 1));
+    if constexpr (H) {
+      const unsigned* x = static_cast<const unsigned*>(xin);
+      R.w[i].a = cx.ldg16x2(x + n);
+      R.w[i].m0 = n > 0 ? cx.ldg16(x + (N - n)) : 0u;
+      R.w[i].m1 = cx.ldg16(x + (N - n - 1));
+    } else {
+      const float2* x = static_cast<const float2*>(xin);
+      R.w[i].a = cx.ldg4(x + n);
+      R.w[i].m0 = n > 0 ? cx.ldg2(x + (N - n)) : make_float2(0.f, 0.f);
+      R.w[i].m1 = cx.ldg2(x + (N - n - 1));
+    }
   }
 }
 
-template <int LN, bool INV, class Ctx>
-PR_HD void load_scatter(Ctx& cx, int r, int round, const LoadRound<LN>& R) {
-  constexpr int N = 1 << LN, Q = N / 4, NT = LoadRound<LN>::NT, NI = LoadRound<LN>::NI;
-  const float cj = INV ? -1.f : 1.f;
+// sample as float2, conjugated for the inverse (16-bit: times 2^exp_in)
+template <bool INV, class Ctx>
+PR_HD float2 sample(Ctx& cx, float2 v, float, int) {
+  return make_float2(v.x, INV ? v.y * -1.f : v.y);
+}
+template <bool INV, class Ctx>
+PR_HD float2 sample(Ctx& cx, unsigned u, float s, int dt) {
+  const float2 v = cx.unpack16(u, dt);
+  return make_float2(v.x * s, v.y * (INV ? s * -1.f : s));
+}
+
+template <int LN, bool INV, bool H, class Ctx>
+PR_HD void load_scatter(Ctx& cx, int r, int round, const LoadRound<LN, H>& R, float s, int dt) {
+  constexpr int N = 1 << LN, Q = N / 4, NT = LoadRound<LN, H>::NT, NI = LoadRound<LN, H>::NI;
 #pragma unroll
   for (int i = 0; i < NI; ++i) {
     const int n = r * (N / 8) + 2 * (cx.tid + (round * NI + i) * NT);
-    const float2 xn = make_float2(R.a[i].x, R.a[i].y * cj), xo = make_float2(R.a[i].z, R.a[i].w * cj);
-    const float2 y0 = make_float2(R.m0[i].x, R.m0[i].y * cj), y1 = make_float2(R.m1[i].x, R.m1[i].y * cj);
+    float2 xn, xo;
+    if constexpr (H) {
+      xn = sample<INV>(cx, R.w[i].a.x, s, dt);
+      xo = sample<INV>(cx, R.w[i].a.y, s, dt);
+    } else {
+      xn = sample<INV>(cx, make_float2(R.w[i].a.x, R.w[i].a.y), s, dt);
+      xo = sample<INV>(cx, make_float2(R.w[i].a.z, R.w[i].a.w), s, dt);
+    }
+    const float2 y0 = sample<INV>(cx, R.w[i].m0, s, dt), y1 = sample<INV>(cx, R.w[i].m1, s, dt);
     // odd sample n+1: tree 0, position n/2
     cx.dst2(0, phys(n >> 1), add2(xo, y1));
     cx.dst2(2, phys(n >> 1), sub2(xo, y1));
@@ -789,12 +868,14 @@ PR_HD void load_scatter(Ctx& cx, int r, int round, const LoadRound<LN>& R) {
 }
 
 // dc(N/2) = x(N/2), the second sample of dct(2) (rank 3, thread 0)
-template <int LN, bool INV, class Ctx>
-PR_HD void load_middle(Ctx& cx, const float2* __restrict__ xin, int r) {
+template <int LN, bool INV, bool H, class Ctx>
+PR_HD void load_middle(Ctx& cx, const void* xin, int r, float s, int dt) {
   constexpr int N = 1 << LN, Q = N / 4;
   if (r == 3 && cx.tid == 0) {
-    const float2 h = cx.ldg2(xin + N / 2);
-    cx.dst2(1, phys(Q), make_float2(h.x, INV ? -h.y : h.y));
+    float2 h;
+    if constexpr (H) h = sample<INV>(cx, cx.ldg16(static_cast<const unsigned*>(xin) + N / 2), s, dt);
+    else h = sample<INV>(cx, cx.ldg2(static_cast<const float2*>(xin) + N / 2), s, dt);
+    cx.dst2(1, phys(Q), h);
   }
 }
 
@@ -807,8 +888,22 @@ PR_HD void load_middle(Ctx& cx, const float2* __restrict__ xin, int r) {
 // DST spectra hold harmonic k at position k - 1, so a thread reads positions
 // k, k+1 (harmonics k+1, k+2) and takes harmonic k from the previous lane.
 // INV: the output is conjugated.
-template <int LN, bool INV, class Ctx>
-PR_HD void store_stage(Ctx& cx, float2* __restrict__ xo, int r) {
+// Shared memory of one CTA: the region (phys(2^T) + 1 float2, rounded up to
+// an even count) and the constants of node sizes 64 .. 2^T (tree 0) or
+// 64 .. 2^(T-1) (rest) as floats.
+template <int T>
+PR_HD constexpr int region_f2() {
+  return ((phys(1 << T) + 1) + 1) & ~1;
+}
+template <int T>
+PR_HD constexpr int smem_bytes() {
+  return region_f2<T>() * 8 + ((1 << T) - 32) * 4;
+}
+
+// The outputs of this CTA's harmonics in the order of the store, handed to
+// put2(i, X(i), X(i+1)) and put1(i, X(i)).
+template <int LN, bool INV, class Ctx, class P2, class P1>
+PR_HD void store_walk(Ctx& cx, int r, P2&& put2, P1&& put1) {
   constexpr int N = 1 << LN, Q = N / 4, NT = 1 << (LN - 7), NALL = (Q / 8) / NT;
   constexpr int NI = NALL < 2 ? NALL : 2;  // pairs in flight per thread (register budget)
   const int tid = cx.tid;
@@ -853,61 +948,109 @@ PR_HD void store_stage(Ctx& cx, float2* __restrict__ xo, int r) {
         X0[0] = make_float2(ck.x, ck.y * cj);
         XN[0] = make_float2(cm.x, cm.y * cj);
       }
-      cx.stg4(xo + k, make_float4(X0[0].x, X0[0].y, X0[1].x, X0[1].y));
-      cx.stg4(xo + (N / 2 + k), make_float4(XN[0].x, XN[0].y, XN[1].x, XN[1].y));
+      put2(k, X0[0], X0[1]);
+      put2(N / 2 + k, XN[0], XN[1]);
       if (k > 0) {
-        cx.stg2(xo + (N - k), XM[0]);
-        cx.stg2(xo + (N / 2 - k), XH[0]);
+        put1(N - k, XM[0]);
+        put1(N / 2 - k, XH[0]);
       }
-      cx.stg2(xo + (N - k - 1), XM[1]);
-      cx.stg2(xo + (N / 2 - k - 1), XH[1]);
+      put1(N - k - 1, XM[1]);
+      put1(N / 2 - k - 1, XH[1]);
     }
   }
   if (r == 0 && tid == 0) {
     const float2 cq = cx.dld2(1, phys(Q)), sq = cx.dld2(2, phys(Q - 1));  // C(N/4) = E(N/4), S(N/4) = O(N/4)
-    cx.stg2(xo + Q, make_float2(cq.x + sq.y, (cq.y - sq.x) * cj));
-    cx.stg2(xo + 3 * Q, make_float2(cq.x - sq.y, (cq.y + sq.x) * cj));
+    put1(Q, make_float2(cq.x + sq.y, (cq.y - sq.x) * cj));
+    put1(3 * Q, make_float2(cq.x - sq.y, (cq.y + sq.x) * cj));
   }
 }
 
-// Shared memory of one CTA: the region (phys(2^T) + 1 float2, rounded up to
-// an even count) and the constants of node sizes 64 .. 2^T (tree 0) or
-// 64 .. 2^(T-1) (rest) as floats.
-template <int T>
-PR_HD constexpr int region_f2() {
-  return ((phys(1 << T) + 1) + 1) & ~1;
+PR_HD float absmax2(float m, float2 v) {
+  const float a = v.x < 0.f ? -v.x : v.x, b = v.y < 0.f ? -v.y : v.y;
+  m = a > m ? a : m;  // a NaN never wins (as fmaxf)
+  return b > m ? b : m;
 }
-template <int T>
-PR_HD constexpr int smem_bytes() {
-  return region_f2<T>() * 8 + ((1 << T) - 32) * 4;
+
+// Store: the last chain level (M = N) from the four CTAs, D_r^F (R = DCT - i
+// DST, Eq. qft_24-25) and D_c^F (Eq. qft_17-21):
+//   X(k) = (C1 + S2, C2 - S1),  X(N-k) = (C1 - S2, C2 + S1)  at k and N/2 - k,
+// harmonics k in [r Q/4, (r+1) Q/4), a pair (k, k+1) per thread and step,
+// and X(N/4), X(3N/4) (rank 0).  Every read is one 16-byte run of
+// distributed shared memory, consecutive lanes reading consecutive runs: the
+// DST spectra hold harmonic k at position k - 1, so a thread reads positions
+// k, k+1 (harmonics k+1, k+2) and takes harmonic k from the previous lane.
+// INV: the output is conjugated.  16-bit (H): a first walk takes the largest
+// component magnitude (the CTA's through the Ctx, the cluster's through the
+// spare word of each region), which fixes the transform's exponent; the
+// second walk scales by 2^-exp and rounds.
+template <int LN, bool INV, bool H, class Ctx>
+PR_HD void store_stage(Ctx& cx, void* xo, int r, const Store16* io, long long t) {
+  if constexpr (!H) {
+    float2* z = static_cast<float2*>(xo);
+    store_walk<LN, INV>(
+        cx, r, [&](int i, float2 a, float2 b) { cx.stg4(z + i, make_float4(a.x, a.y, b.x, b.y)); },
+        [&](int i, float2 a) { cx.stg2(z + i, a); });
+  } else {
+    constexpr int SPARE = region_f2<LN - 2>() - 1;
+    float m = 0.f;
+    store_walk<LN, INV>(
+        cx, r, [&](int, float2 a, float2 b) { m = absmax2(absmax2(m, a), b); },
+        [&](int, float2 a) { m = absmax2(m, a); });
+    m = cx.max_cta(m);
+    if (cx.tid == 0) cx.dst2(r, SPARE, make_float2(m, 0.f));
+    cx.sync_cluster();
+    float M = 0.f;
+    for (int q = 0; q < 4; ++q) {
+      const float v = cx.dld2(q, SPARE).x;
+      M = v > M ? v : M;
+    }
+    const int e = block_exp(M);
+    const float sc = pow2_exact(-e);
+    const int dt = io->dtype;
+    if (r == 0 && cx.tid == 0) io->exp_out[t] = e;
+    unsigned* z = static_cast<unsigned*>(xo);
+    store_walk<LN, INV>(
+        cx, r,
+        [&](int i, float2 a, float2 b) {
+          cx.stg16x2(z + i, make_uint2(cx.pack16(a.x * sc, a.y * sc, dt), cx.pack16(b.x * sc, b.y * sc, dt)));
+        },
+        [&](int i, float2 a) { cx.stg16(z + i, cx.pack16(a.x * sc, a.y * sc, dt)); });
+  }
 }
 
 // The cluster's work: transforms cid, cid + ncl, ... of the batch (batch below
 // 2^31; the dispatch checks it).
 // reg: this CTA's region; Ctx reaches CTA q's region with dst2 / dld2 / dld4
 // (float2 index into the region: distributed shared memory for the others).
-template <int LN, bool INV, class Ctx>
-PR_HD void paired_body(Ctx& cx, const float2* __restrict__ in, float2* __restrict__ out, int batch, int cid,
-                       int ncl, float2* reg, float* __restrict__ cst,
-                       const float* __restrict__ ctab, const LeafConsts& K) {
+template <int LN, bool INV, bool H, class Ctx>
+PR_HD void paired_body(Ctx& cx, const void* in, void* out, const Store16* io, int batch, int cid, int ncl,
+                       float2* reg, float* __restrict__ cst, const float* __restrict__ ctab, const LeafConsts& K) {
   constexpr int T = LN - 2, NT = 1 << (T - 5);
   constexpr long long N = 1LL << LN;
+  constexpr int ES = H ? 4 : 8;  // bytes per element in HBM
   const int r = cx.rank, tid = cx.tid;
   const int ncst = (r & 1) == 0 ? (1 << T) - 32 : (1 << (T - 1)) - 32;
   if (ctab)  // else the kernel has evaluated them on the fly
     for (int i = tid; i < ncst; i += NT) cst[i] = ctab[30 + i];
-  LoadRound<LN> R;
-  if (cid < batch) load_fetch<LN>(cx, in + (long long)cid * N, r, 0, R);
+  const int dt = H ? io->dtype : 0;
+  auto at = [&](const void* base, long long t) {
+    return static_cast<const void*>(static_cast<const char*>(base) + t * N * ES);
+  };
+  // 2^exp_in of transform t (16-bit input)
+  auto scale = [&](long long t) { return H && io->exp_in ? pow2_exact(io->exp_in[t]) : 1.f; };
+  LoadRound<LN, H> R;
+  if (cid < batch) load_fetch<LN, H>(cx, at(in, cid), r, 0, R);
   for (int t = cid; t < batch; t += ncl) {
-    const float2* xin = in + (long long)t * N;
+    const void* xin = at(in, t);
+    const float s = scale(t);
     cx.sync_cluster();  // the previous store has read every region
-    load_scatter<LN, INV>(cx, r, 0, R);
+    load_scatter<LN, INV, H>(cx, r, 0, R, s, dt);
 #pragma unroll
     for (int rd = 1; rd < 4; ++rd) {
-      load_fetch<LN>(cx, xin, r, rd, R);
-      load_scatter<LN, INV>(cx, r, rd, R);
+      load_fetch<LN, H>(cx, xin, r, rd, R);
+      load_scatter<LN, INV, H>(cx, r, rd, R, s, dt);
     }
-    load_middle<LN, INV>(cx, xin, r);
+    load_middle<LN, INV, H>(cx, xin, r, s, dt);
     cx.sync_cluster();
     switch (r) {
       case 0: cta_transform<T, 0, true>(cx, reg, cst, K); break;
@@ -916,9 +1059,9 @@ PR_HD void paired_body(Ctx& cx, const float2* __restrict__ in, float2* __restric
       default: cta_transform<T, 1, false>(cx, reg, cst, K); break;
     }
     cx.sync_cluster();
-    store_stage<LN, INV>(cx, out + (long long)t * N, r);
+    store_stage<LN, INV, H>(cx, const_cast<void*>(at(out, t)), r, io, t);
     // the next transform's first reads fly across the barrier at the loop top
-    if (t + ncl < batch) load_fetch<LN>(cx, in + (long long)(t + ncl) * N, r, 0, R);
+    if (t + ncl < batch) load_fetch<LN, H>(cx, at(in, t + ncl), r, 0, R);
   }
   cx.sync_cluster();  // keep the regions alive for the other CTAs' reads
 }

@@ -7,13 +7,15 @@
 // Built with AddressSanitizer by the test, so an index outside a region, a
 // constant table or a buffer is reported on the CPU.
 //
-// usage: paired_emu <inverse 0|1> <batch> <in.bin> <out.bin>   (N = 2^PAIRED_LN)
+// usage: paired_emu <inverse 0|1> <batch> <in.bin> <out.bin> [<dtype> <exp_in.bin> <exp_out.bin>]
+// (N = 2^PAIRED_LN; dtype 1 bf16, 2 fp16, 3 int16 storage, else complex64)
 #include <cuda_runtime.h>
 
 #include <barrier>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <cstring>
 #include <memory>
 #include <thread>
 #include <vector>
@@ -38,6 +40,65 @@ struct HostCtx {
   float2 ldg2(const float2* p) { return *p; }
   void stg4(float2* p, float4 v) { *reinterpret_cast<float4*>(p) = v; }
   void stg2(float2* p, float2 v) { *p = v; }
+  uint2 ldg16x2(const unsigned* p) { return make_uint2(p[0], p[1]); }
+  unsigned ldg16(const unsigned* p) { return *p; }
+  void stg16x2(unsigned* p, uint2 v) {
+    p[0] = v.x;
+    p[1] = v.y;
+  }
+  void stg16(unsigned* p, unsigned v) { *p = v; }
+  // 16-bit conversions (round to nearest even), as the device's
+  static float bits(uint32_t u) {
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+  }
+  static uint32_t ubits(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return u;
+  }
+  static unsigned to16(float v, int dt) {
+    if (dt == 1) {
+      uint32_t u = ubits(v);
+      if ((u & 0x7fffffffu) > 0x7f800000u) return 0x7fc0u;
+      u += 0x7fffu + ((u >> 16) & 1u);
+      return u >> 16;
+    }
+    if (dt == 3) {
+      float q = std::nearbyint(v);
+      q = q < -32768.f ? -32768.f : (q > 32767.f ? 32767.f : q);
+      return (unsigned)(unsigned short)(short)q;
+    }
+    const uint32_t x = ubits(v), sign = (x >> 16) & 0x8000u, ax = x & 0x7fffffffu;
+    if (ax >= 0x7f800000u) return sign | (ax > 0x7f800000u ? 0x7e00u : 0x7c00u);
+    if (ax >= 0x477ff000u) return sign | 0x7c00u;  // rounds to infinity
+    if (ax < 0x38800000u) return sign | (uint32_t)std::nearbyint(bits(ax) * 16777216.0f);  // subnormal
+    uint32_t h = ((((ax >> 23) - 127 + 15) << 10) | ((ax & 0x7fffffu) >> 13));
+    const uint32_t rem = ax & 0x1fffu;
+    if (rem > 0x1000u || (rem == 0x1000u && (h & 1u))) ++h;
+    return sign | h;
+  }
+  static float from16(unsigned h, int dt) {
+    if (dt == 1) return bits(h << 16);
+    if (dt == 3) return (float)(short)(unsigned short)h;
+    const uint32_t sign = (h & 0x8000u) << 16, e = (h >> 10) & 31u, m = h & 1023u;
+    if (e == 0) return bits(sign) + (sign ? -1.f : 1.f) * (float)m * (1.0f / 16777216.0f);
+    if (e == 31) return bits(sign | 0x7f800000u | (m << 13));
+    return bits(sign | ((e - 15 + 127) << 23) | (m << 13));
+  }
+  float2 unpack16(unsigned u, int dt) { return make_float2(from16(u & 0xffffu, dt), from16(u >> 16, dt)); }
+  unsigned pack16(float re, float im, int dt) { return to16(re, dt) | (to16(im, dt) << 16); }
+  float* cred;  // this CTA's max slots
+  float max_cta(float m) {
+    cred[tid] = m;
+    bcta->arrive_and_wait();
+    float r = 0.f;
+    for (int i = 0; i < nth; ++i) r = cred[i] > r ? cred[i] : r;
+    bcta->arrive_and_wait();
+    return r;
+  }
+  int nth;
   float2 shfl_up(float2 v, int d) {
     const int ln = tid & 31;
     wslot[ln] = v;
@@ -71,8 +132,8 @@ long double cos_turn(long long num, long long den) {
   return sign * cosl(two_pi * (long double)r / (long double)den);
 }
 
-template <int LN, bool INV>
-void run(const float2* in, float2* out, long long batch) {
+template <int LN, bool INV, bool H>
+void run(const void* in, void* out, const Store16* io, long long batch) {
   constexpr int T = LN - 2, NT = 1 << (T - 5), N = 1 << LN;
   std::vector<float> ctab(N / 4 - 2);
   for (long long M = 16; M <= N; M *= 2)
@@ -90,13 +151,16 @@ void run(const float2* in, float2* out, long long batch) {
   for (int q = 0; q < 4; ++q) bcta.emplace_back(new std::barrier<>(NT));
   for (int w = 0; w < 4 * NT / 32; ++w) bwarp.emplace_back(new std::barrier<>(32));
   std::vector<float2> slots(4 * NT);
+  std::vector<float> red(4 * NT);
   std::vector<std::thread> th;
   for (int q = 0; q < 4; ++q)
     for (int t = 0; t < NT; ++t)
       th.emplace_back([&, q, t]() {
         HostCtx cx{t, q, &bcl, bcta[q].get(), bwarp[q * (NT / 32) + t / 32].get(), &slots[(q * NT + t) & ~31], regs};
+        cx.cred = &red[q * NT];
+        cx.nth = NT;
         float* cst = reinterpret_cast<float*>(regs[q] + region_f2<T>());
-        paired_body<LN, INV>(cx, in, out, batch, 0, 1, regs[q], cst, ctab.data(), K);
+        paired_body<LN, INV, H>(cx, in, out, io, (int)batch, 0, 1, regs[q], cst, ctab.data(), K);
       });
   for (auto& x : th) x.join();
 }
@@ -104,18 +168,38 @@ void run(const float2* in, float2* out, long long batch) {
 }  // namespace
 
 int main(int argc, char** argv) {
-  if (argc != 5) return 2;
+  // paired_emu <inverse> <batch> <in.bin> <out.bin> [dtype exp_in.bin exp_out.bin]
+  if (argc != 5 && argc != 8) return 2;
   const int inv = atoi(argv[1]);
   const long long batch = atoll(argv[2]);
   const long long N = 1LL << PAIRED_LN;
-  std::vector<float2> in(N * batch), out(N * batch, make_float2(NAN, NAN));
+  const int dt = argc == 8 ? atoi(argv[5]) : 0;
+  const size_t es = dt ? 4 : 8;
+  std::vector<unsigned char> in(N * batch * es), out(N * batch * es, 0xff);
   FILE* f = fopen(argv[3], "rb");
-  if (!f || fread(in.data(), sizeof(float2), in.size(), f) != in.size()) return 3;
+  if (!f || fread(in.data(), 1, in.size(), f) != in.size()) return 3;
   fclose(f);
-  if (inv) run<PAIRED_LN, true>(in.data(), out.data(), batch);
-  else run<PAIRED_LN, false>(in.data(), out.data(), batch);
+  std::vector<int> ein(batch, 0), eout(batch, 0);
+  if (dt) {
+    f = fopen(argv[6], "rb");
+    if (!f || fread(ein.data(), sizeof(int), ein.size(), f) != ein.size()) return 3;
+    fclose(f);
+  }
+  const Store16 io{ein.data(), eout.data(), dt};
+  if (dt) {
+    if (inv) run<PAIRED_LN, true, true>(in.data(), out.data(), &io, batch);
+    else run<PAIRED_LN, false, true>(in.data(), out.data(), &io, batch);
+  } else {
+    if (inv) run<PAIRED_LN, true, false>(in.data(), out.data(), nullptr, batch);
+    else run<PAIRED_LN, false, false>(in.data(), out.data(), nullptr, batch);
+  }
   f = fopen(argv[4], "wb");
-  if (!f || fwrite(out.data(), sizeof(float2), out.size(), f) != out.size()) return 4;
+  if (!f || fwrite(out.data(), 1, out.size(), f) != out.size()) return 4;
   fclose(f);
+  if (dt) {
+    f = fopen(argv[7], "wb");
+    if (!f || fwrite(eout.data(), sizeof(int), eout.size(), f) != eout.size()) return 4;
+    fclose(f);
+  }
   return 0;
 }

@@ -62,3 +62,45 @@ def test_paired_emulation_2e14(orc, emu_binary, inverse, tmp_path):
 @pytest.mark.parametrize("log2n", [15, 16])
 def test_paired_emulation_larger(orc, emu_binary, log2n, tmp_path):
     _run(orc, emu_binary(log2n), log2n, 2, log2n == 16, tmp_path)
+
+
+def _run16(orc, binary, log2n, batch, dt, tmp_path):
+    """16-bit storage (dt 1 bf16, 3 int16): forward from exponent-0 input,
+    then the inverse of that output with its exponents; every value and
+    exponent must equal the oracle's float32 recursion rounded the same way."""
+    import torch
+
+    from gpu_util import expected_exponent
+
+    n = 1 << log2n
+    x = synth.normal_complex(n, batch, config=2, stream=720 + log2n)
+    t = torch.view_as_real(torch.from_numpy(np.ascontiguousarray(x)))
+    to16 = (lambda v: (v * 4096.0).round().to(torch.int16)) if dt == 3 else (lambda v: v.to(torch.bfloat16))
+    x16 = to16(t).contiguous()
+    env = dict(os.environ, ASAN_OPTIONS="detect_leaks=0:detect_stack_use_after_return=0")
+    e_in = np.zeros(batch, dtype=np.int32)
+    for inverse in (False, True):
+        fi, fo = str(tmp_path / "in16.bin"), str(tmp_path / "out16.bin")
+        ei, eo = str(tmp_path / "ein.bin"), str(tmp_path / "eout.bin")
+        x16.view(torch.int16).numpy().tofile(fi)
+        e_in.tofile(ei)
+        r = subprocess.run([binary, str(int(inverse)), str(batch), fi, fo, str(dt), ei, eo], capture_output=True,
+                           text=True, env=env, timeout=900)
+        assert r.returncode == 0, r.stderr[-2000:]
+        y16 = torch.from_numpy(np.fromfile(fo, dtype=np.int16).reshape(batch, n, 2).copy())
+        e_out = np.fromfile(eo, dtype=np.int32)
+        xin = torch.view_as_complex(x16.double().contiguous()).numpy() * (2.0 ** e_in)[:, None]
+        for b in range(batch):
+            r32 = orc.amqft(xin[b], 4, prec="f32", sign=+1 if inverse else -1).astype(np.complex64)
+            ee = expected_exponent(r32)
+            assert int(e_out[b]) == ee, (dt, inverse, b, int(e_out[b]), ee)
+            scaled = torch.view_as_real(torch.from_numpy((r32 * np.float32(2.0 ** -ee)).astype(np.complex64)))
+            want = (scaled.round().to(torch.int16) if dt == 3 else scaled.to(torch.bfloat16)).view(torch.int16)
+            assert torch.equal(y16[b], want), (dt, inverse, b)
+        x16 = y16.view(torch.bfloat16) if dt == 1 else y16
+        e_in = e_out.astype(np.int32)
+
+
+@pytest.mark.parametrize("dt", [1, 3])
+def test_paired_emulation_16bit(orc, emu_binary, dt, tmp_path):
+    _run16(orc, emu_binary(14), 14, 2, dt, tmp_path)

@@ -455,6 +455,7 @@ __device__ __forceinline__ void store_emit(float2* __restrict__ out, int logN, l
   const Out4 o = emit_values<V>(logN, k, g);
   float2* __restrict__ z = out + off;
   const int N = 1 << logN;
+  (void)N;  // the bound of the checked build
 #pragma unroll
   for (int j = 0; j < 4; ++j)
     if (o.i[j] >= 0 && AMQFT_IN_BOUNDS(o.i[j], N, BS_HBM_OUT)) stz(z, o.i[j], o.v[j].x, o.v[j].y, cj);

@@ -11,10 +11,11 @@
 //            passes (chunk totals, a scan of the totals per node, the chunks
 //            re-run with their carries), and chain levels of periodisation
 //            > 4S one per pass;
-//   solve    one CTA per pair of tree nodes of size S (node mode) and one per
-//            region tail (the trees of size <= S plus the chain up to 4S, a
-//            region of N' = 4S) in shared memory, with the fused kernel's
-//            bands, register subtrees and passes;
+//   solve    one CTA per tree node of size 2S (node mode: its two children of
+//            size S and its own M_v relation) and one per region tail (the
+//            trees of size <= S plus the chain up to 4S, a region of N' = 4S)
+//            in shared memory, with the fused kernel's bands, register
+//            subtrees and passes;
 //   store    last chain level (time-first variants), D_r^F and D_c^F.
 //
 // The recurrence variants (1, 3, 5, 7) take the scans without any wait
@@ -425,8 +426,8 @@ __global__ void mp_chain_kernel(MpArgs a, const float* __restrict__ Win, float* 
   }
 }
 
-// Subproblem solve.  Blocks [0, nnode/2) of each region take two tree nodes
-// of size S each (node mode), the last block the region tail (region mode,
+// Subproblem solve.  Blocks [0, nnode/2) of each region take one tree node of
+// size 2S each (node mode), the last block the region tail (region mode,
 // N' = 4S).  The words are copied verbatim: S and half - 2S are multiples of
 // 1024, so the swizzle of the workspace and of shared memory coincide.
 template <int V, int TPB>
@@ -452,36 +453,34 @@ __global__ void __launch_bounds__(TPB) mp_solve_kernel(MpArgs a, float* W, const
   const TabConsts cs{cst};
   Geo g;
   if (sidx < nnode / 2) {
-    // node mode: nodes 2*sidx and 2*sidx + 1
-    const int n0 = 2 * sidx;
-    int mask = 0;
-    for (int j = 0; j < 2; ++j) {
-      const int p0 = (n0 + j) << MP_LOG_S;
-      mask |= node_ctx<V>(p0, MP_LOG_S, half, ctx0) << j;
-      for (int e = threadIdx.x; e < MP_S; e += TPB) sm[j * RSn + e] = R[p0 + e];
-    }
-    g.logN = MP_LOG_S + 2;
-    g.half = MP_S;
-    g.RS = RSn;
-    g.nreg = 2;
-    g.nreg_cap = 2;
-    g.gbase = mask;
-    g.sub = MP_S;
+    // node mode: the tree node of size 2S at 2S * sidx (children 2*sidx and
+    // 2*sidx + 1 of size S), its levels up to and including its own M_v
+    // relation (the frequency phase last for the time-first variants, the
+    // time phase first for the harmonics-first ones)
+    const int L2 = 2 * MP_S, P = sidx * L2;
+    for (int e = threadIdx.x; e < L2; e += TPB) sm[e] = R[P + e];
+    g.logN = MP_LOG_S + 3;
+    g.half = L2;
+    g.RS = L2;
+    g.nreg = 1;
+    g.nreg_cap = 1;
+    g.gbase = node_ctx<V>(P, MP_LOG_S + 1, half, ctx0);
+    g.sub = L2;
     __syncthreads();
-    const BandPlan bp = band_plan(MP_LOG_S + 2);
-    const int nleaf = MP_S >> LOG_LEAF;
+    const BandPlan bp = band_plan(MP_LOG_S + 2);  // levels S .. 2*LEAF
+    const int nleaf = L2 >> LOG_LEAF;
     if constexpr (Var<V>::ot) {
       for (int b = 0; b < bp.nb; ++b) {
         run_fold_band_r<V, TPB>(sm, g, bp.logL[b], bp.R[b], true, cs);
         __syncthreads();
       }
-      for (int w = threadIdx.x; w < 2 * nleaf; w += TPB) {
-        const int r = w / nleaf, p0 = (w - r * nleaf) << LOG_LEAF;
-        run_leaf<V>(reg_ptr(sm + r * RSn, RSn), p0, node_ctx_g<V>(g, p0, LOG_LEAF, ctx_of(g, r)), K);
+      for (int w = threadIdx.x; w < nleaf; w += TPB) {
+        const int p0 = w << LOG_LEAF;
+        run_leaf<V>(reg_ptr(sm, L2), p0, node_ctx_g<V>(g, p0, LOG_LEAF, ctx_of(g, 0)), K);
       }
       __syncthreads();
       if constexpr (Var<V>::scan) {
-        for (int lp = LOG_LEAF + 1; lp <= MP_LOG_S; ++lp) {
+        for (int lp = LOG_LEAF + 1; lp <= MP_LOG_S + 1; ++lp) {
           pass_recurrence<V, TPB, 16>(sm, tot, wsum, g, lp);
           __syncthreads();
         }
@@ -490,16 +489,18 @@ __global__ void __launch_bounds__(TPB) mp_solve_kernel(MpArgs a, float* W, const
           run_chunk_band_r<V, TPB>(sm, snap, g, bp.logL[b], bp.R[b]);
           __syncthreads();
         }
+        pass_neighbour<V, TPB, 16>(sm, g, MP_LOG_S + 1);
+        __syncthreads();
       }
     } else {
-      for (int lp = MP_LOG_S; lp >= LOG_LEAF + 1; --lp) {
+      for (int lp = MP_LOG_S + 1; lp >= LOG_LEAF + 1; --lp) {
         if constexpr (Var<V>::scan) pass_recurrence<V, TPB, 16>(sm, tot, wsum, g, lp);
         else pass_neighbour<V, TPB, 16>(sm, g, lp);
         __syncthreads();
       }
-      for (int w = threadIdx.x; w < 2 * nleaf; w += TPB) {
-        const int r = w / nleaf, p0 = (w - r * nleaf) << LOG_LEAF;
-        run_leaf<V>(reg_ptr(sm + r * RSn, RSn), p0, node_ctx_g<V>(g, p0, LOG_LEAF, ctx_of(g, r)), K);
+      for (int w = threadIdx.x; w < nleaf; w += TPB) {
+        const int p0 = w << LOG_LEAF;
+        run_leaf<V>(reg_ptr(sm, L2), p0, node_ctx_g<V>(g, p0, LOG_LEAF, ctx_of(g, 0)), K);
       }
       __syncthreads();
       for (int b = bp.nb - 1; b >= 0; --b) {
@@ -507,10 +508,7 @@ __global__ void __launch_bounds__(TPB) mp_solve_kernel(MpArgs a, float* W, const
         __syncthreads();
       }
     }
-    for (int j = 0; j < 2; ++j) {
-      const int p0 = (n0 + j) << MP_LOG_S;
-      for (int e = threadIdx.x; e < MP_S; e += TPB) R[p0 + e] = sm[j * RSn + e];
-    }
+    for (int e = threadIdx.x; e < L2; e += TPB) R[P + e] = sm[e];
   } else {
     // tail: region of N' = 4S at [half - 2S, RSg)
     const int base = half - 2 * MP_S;
@@ -652,7 +650,7 @@ cudaError_t mp_run(const MpArgs& a0, float* W0, float* W1, const SmallConsts& K,
       if ((e = fold(b, true)) != cudaSuccess) return e;
     mp_solve_kernel<V, MP_TPB><<<nsolve, MP_TPB, smem, st>>>(a, cur, K);
     if ((e = launched()) != cudaSuccess) return e;
-    for (int lp = MP_LOG_S + 1; lp <= logN - 2; ++lp)
+    for (int lp = MP_LOG_S + 2; lp <= logN - 2; ++lp)  // 2^(S+1): in the solve
       if ((e = relation(lp)) != cudaSuccess) return e;
     for (int lm = MP_LOG_S + 3; lm <= logN - 1; ++lm) {
       mp_chain_kernel<V><<<grid_for(words), threads, 0, st>>>(a, cur, oth, lm);
@@ -665,7 +663,7 @@ cudaError_t mp_run(const MpArgs& a0, float* W0, float* W1, const SmallConsts& K,
       if ((e = launched()) != cudaSuccess) return e;
       float* t = cur; cur = oth; oth = t;
     }
-    for (int lp = logN - 2; lp >= MP_LOG_S + 1; --lp)
+    for (int lp = logN - 2; lp >= MP_LOG_S + 2; --lp)  // 2^(S+1): in the solve
       if ((e = relation(lp)) != cudaSuccess) return e;
     mp_solve_kernel<V, MP_TPB><<<nsolve, MP_TPB, smem, st>>>(a, cur, K);
     if ((e = launched()) != cudaSuccess) return e;

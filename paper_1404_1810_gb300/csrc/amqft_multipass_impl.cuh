@@ -223,6 +223,68 @@ __global__ void mp_neighbour_kernel(MpArgs a, const float* __restrict__ Win, flo
   }
 }
 
+// The neighbour form's output at position p for node size 2^logLp, from its
+// input R (the value itself where p is not in a class-0 B half).
+template <int V>
+__device__ __forceinline__ float nb_at(CRegP R, int p, int logLp, int half, int ctx0) {
+  const float v = R[sw(p)];
+  const int Lp = 1 << logLp, H = Lp >> 1, h = logLp - 1;
+  if (p >= half - Lp) return v;
+  const int p0 = p & ~(Lp - 1);
+  const int ctx = node_ctx<V>(p0, logLp, half, ctx0);
+  const int base = ctx == 0 ? p0 + H : p0;
+  if (p < base || p >= base + H) return v;
+  const int i = brev(p - base, h);
+  int dir;
+  bool add;
+  if constexpr (V == 4) { dir = ctx == 0 ? +1 : -1; add = true; }
+  else if constexpr (V == 8) { dir = ctx == 0 ? -1 : +1; add = false; }
+  else if constexpr (V == 2) { dir = ctx == 0 ? -1 : +1; add = true; }
+  else { dir = ctx == 0 ? +1 : -1; add = false; }
+  const int jn = i + dir;
+  if (jn < 0 || jn >= H) return v;
+  const float bn = R[sw(base + brev(jn, h))];
+  return add ? ((dir > 0) ? (v + bn) : (bn + v)) : (v - bn);
+}
+
+// Two levels of the time-first neighbour relation (M4 / M8 frequency phase,
+// node sizes 2^logLp and 2^(logLp+1)) in one gather pass: each output of the
+// upper level takes the lower level's outputs at its position and at its
+// neighbour's, evaluated from Win on the fly; the same float32 operations as
+// two single-level passes.
+template <int V>
+__global__ void mp_neighbour2_kernel(MpArgs a, const float* __restrict__ Win, float* __restrict__ Wout, int logLp) {
+  static_assert(Var<V>::ot && !Var<V>::scan, "the time-first neighbour form");
+  const int half = 1 << (a.logN - 1), l2 = logLp + 1, L2 = 1 << l2, H2 = L2 >> 1, h2 = l2 - 1;
+  const long long total = a.RSg * 4 * mp_nt(a);
+  for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
+    const long long rr = w / a.RSg;
+    const int ph = (int)(w - rr * a.RSg);
+    const int p = sw(ph);
+    CRegP R = creg_ptr(Win + rr * a.RSg, (int)a.RSg);
+    const int ctx0 = (int)(rr & 1);
+    float v = nb_at<V>(R, p, logLp, half, ctx0);
+    if (p < half - L2) {
+      const int p0 = p & ~(L2 - 1);
+      const int ctx = node_ctx<V>(p0, l2, half, ctx0);
+      const int base = ctx == 0 ? p0 + H2 : p0;
+      if (p >= base && p < base + H2) {
+        const int i = brev(p - base, h2);
+        int dir;
+        bool add;
+        if constexpr (V == 4) { dir = ctx == 0 ? +1 : -1; add = true; }
+        else { dir = ctx == 0 ? -1 : +1; add = false; }  // V == 8
+        const int jn = i + dir;
+        if (jn >= 0 && jn < H2) {
+          const float bn = nb_at<V>(R, base + brev(jn, h2), logLp, half, ctx0);
+          v = add ? ((dir > 0) ? (v + bn) : (bn + v)) : (v - bn);
+        }
+      }
+    }
+    Wout[rr * a.RSg + ph] = v;
+  }
+}
+
 // Recurrence form of M_v on the B halves at node size 2^logLp > S: the
 // frequency phase of M1/M5 (ot variants, the first value halved) or the time
 // phase of M3/M7 (to variants, the last value halved), Tab. 5-6.  A node's B
@@ -420,6 +482,66 @@ __global__ void mp_chain_kernel(MpArgs a, const float* __restrict__ Win, float* 
           const int n = rel - Q + 1;
           v = R[sw(P + n - 1)] - R[sw(P + M / 2 - n - 1)];
         }
+      }
+    }
+    Wout[rr * a.RSg + ph] = v;
+  }
+}
+
+// Two chain levels of the time-first variants in one gather pass: the D_n
+// frequency phase of periodisation M = 2^logM and then of 2M.  Level 2M
+// writes the whole range level M writes (its E input is level M's output),
+// so each of its outputs takes its E value from level M's formula applied to
+// Win on the fly (two more reads, from cache) and its O value (the 2M tree)
+// from Win; every other word is copied.  Same float32 operations per output
+// as the two single-level passes.
+template <int V>
+__device__ __forceinline__ float chain_ot_value(CRegP R, int ctx0, int P, int Q, int logQ, int M, int rel) {
+  // level M's output at P + rel, from its inputs in R (rel inside its range)
+  if (ctx0 == 0) {
+    if (rel == Q) return R[sw(P + 2 * Q)];
+    const int k = rel < Q ? rel : M / 2 - rel;
+    const float e = R[sw(P + Q + k)], o = R[sw(P + brev(k, logQ))];
+    return rel < Q ? (e + o) : (e - o);
+  }
+  const int k = rel + 1;
+  if (k == Q) return R[sw(P + Q - 1)];
+  const int kk = k < Q ? k : M / 2 - k;
+  const float o = R[sw(P + brev(kk - 1, logQ))], e = R[sw(P + Q + kk - 1)];
+  return k < Q ? (o + e) : (o - e);
+}
+
+template <int V>
+__global__ void mp_chain2_kernel(MpArgs a, const float* __restrict__ Win, float* __restrict__ Wout, int logM) {
+  static_assert(Var<V>::ot, "the time-first chain");
+  const int half = 1 << (a.logN - 1);
+  const int M = 1 << logM, logQ = logM - 2, Q = 1 << logQ, P = half - M / 2;          // level M
+  const int M2 = 2 * M, logQ2 = logQ + 1, Q2 = 2 * Q, P2 = half - M;                  // level 2M
+  const long long total = a.RSg * 4 * mp_nt(a);
+  for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
+    const long long rr = w / a.RSg;
+    const int ph = (int)(w - rr * a.RSg);
+    const int p = sw(ph);
+    CRegP R = creg_ptr(Win + rr * a.RSg, (int)a.RSg);
+    const int ctx0 = (int)(rr & 1);
+    float v = R[ph];
+    const int rel2 = p - P2;
+    if (ctx0 == 0 && rel2 >= 0 && rel2 <= M2 / 2) {
+      if (rel2 == Q2) {
+        v = chain_ot_value<V>(R, 0, P, Q, logQ, M, 2 * Q);  // E2(Q2): level M at its harmonic M/2
+      } else {
+        const int k2 = rel2 < Q2 ? rel2 : M2 / 2 - rel2;
+        const float e = chain_ot_value<V>(R, 0, P, Q, logQ, M, k2), o = R[sw(P2 + brev(k2, logQ2))];
+        v = rel2 < Q2 ? (e + o) : (e - o);
+      }
+    } else if (ctx0 == 1 && rel2 >= 0 && rel2 < M2 / 2 - 1) {
+      const int k2 = rel2 + 1;
+      if (k2 == Q2) {
+        v = R[sw(P2 + Q2 - 1)];
+      } else {
+        const int kk = k2 < Q2 ? k2 : M2 / 2 - k2;
+        const float o = R[sw(P2 + brev(kk - 1, logQ2))], e = chain_ot_value<V>(R, 1, P, Q, logQ, M, kk - 1);
+        v = k2 < Q2 ? (o + e) : (o - e);
       }
     }
     Wout[rr * a.RSg + ph] = v;
@@ -650,10 +772,33 @@ cudaError_t mp_run(const MpArgs& a0, float* W0, float* W1, const SmallConsts& K,
       if ((e = fold(b, true)) != cudaSuccess) return e;
     mp_solve_kernel<V, MP_TPB><<<nsolve, MP_TPB, smem, st>>>(a, cur, K);
     if ((e = launched()) != cudaSuccess) return e;
-    for (int lp = MP_LOG_S + 2; lp <= logN - 2; ++lp)  // 2^(S+1): in the solve
-      if ((e = relation(lp)) != cudaSuccess) return e;
-    for (int lm = MP_LOG_S + 3; lm <= logN - 1; ++lm) {
+    int lp = MP_LOG_S + 2;  // 2^(S+1): in the solve
+    if constexpr (!Var<V>::scan) {
+      // the neighbour levels two a pass, a single one first when their count is odd
+      if (lp <= logN - 2 && ((logN - 2 - lp + 1) & 1)) {
+        if ((e = relation(lp)) != cudaSuccess) return e;
+        ++lp;
+      }
+      for (; lp + 1 <= logN - 2; lp += 2) {
+        mp_neighbour2_kernel<V><<<grid_for(words), threads, 0, st>>>(a, cur, oth, lp);
+        if ((e = launched()) != cudaSuccess) return e;
+        float* t = cur; cur = oth; oth = t;
+      }
+    } else {
+      for (; lp <= logN - 2; ++lp)
+        if ((e = relation(lp)) != cudaSuccess) return e;
+    }
+    // chain levels 2^(S+3) .. 2^(n-1): two a pass, a single one first when
+    // their count is odd
+    int lm = MP_LOG_S + 3;
+    if (((logN - 1) - lm + 1) & 1) {
       mp_chain_kernel<V><<<grid_for(words), threads, 0, st>>>(a, cur, oth, lm);
+      if ((e = launched()) != cudaSuccess) return e;
+      float* t = cur; cur = oth; oth = t;
+      ++lm;
+    }
+    for (; lm + 1 <= logN - 1; lm += 2) {
+      mp_chain2_kernel<V><<<grid_for(words), threads, 0, st>>>(a, cur, oth, lm);
       if ((e = launched()) != cudaSuccess) return e;
       float* t = cur; cur = oth; oth = t;
     }

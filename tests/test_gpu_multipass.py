@@ -220,11 +220,13 @@ def test_multipass_chunked_batch(orc):
 def _mp_launches(log2n, dtype16=False):
     """Kernels of one multi-pass chunk (time-first variant): load, the fold
     bands of the levels 2^(n-2) .. 2^14 (at most four levels a band), the
-    in-shared-memory solve (which also takes the 2^14 level's relation), one
-    neighbour pass per level 2^15 .. 2^(n-2), one chain pass per level
-    2^16 .. 2^(n-1), and the store (16-bit: zero, maximum and scaled store)."""
+    in-shared-memory solve (which also takes the 2^14 level's relation), the
+    neighbour levels 2^15 .. 2^(n-2) and the chain levels 2^16 .. 2^(n-1),
+    each two a pass (a single one first when their count is odd), and the
+    store (16-bit: zero, maximum and scaled store)."""
     levels = log2n - 15
-    return 1 + (levels + 3) // 4 + 1 + (levels - 1) + (log2n - 16) + (3 if dtype16 else 1)
+    nb = chain = log2n - 16
+    return 1 + (levels + 3) // 4 + 1 + (nb + 1) // 2 + (chain + 1) // 2 + (3 if dtype16 else 1)
 
 
 def test_launch_count():

@@ -223,6 +223,16 @@ __global__ void mp_neighbour_kernel(MpArgs a, const float* __restrict__ Win, flo
   }
 }
 
+// Which neighbour (+1 / -1 in bit-reversed order) enters, and whether it is
+// added or subtracted: M4 / M8 frequency phase, M2 / M6 time phase.
+template <int V>
+__device__ __forceinline__ void nb_rule(int ctx, int& dir, bool& add) {
+  if constexpr (V == 4) { dir = ctx == 0 ? +1 : -1; add = true; }
+  else if constexpr (V == 8) { dir = ctx == 0 ? -1 : +1; add = false; }
+  else if constexpr (V == 2) { dir = ctx == 0 ? -1 : +1; add = true; }
+  else { dir = ctx == 0 ? +1 : -1; add = false; }  // V == 6
+}
+
 // The neighbour form's output at position p for node size 2^logLp, from its
 // input R (the value itself where p is not in a class-0 B half).
 template <int V>
@@ -237,25 +247,24 @@ __device__ __forceinline__ float nb_at(CRegP R, int p, int logLp, int half, int 
   const int i = brev(p - base, h);
   int dir;
   bool add;
-  if constexpr (V == 4) { dir = ctx == 0 ? +1 : -1; add = true; }
-  else if constexpr (V == 8) { dir = ctx == 0 ? -1 : +1; add = false; }
-  else if constexpr (V == 2) { dir = ctx == 0 ? -1 : +1; add = true; }
-  else { dir = ctx == 0 ? +1 : -1; add = false; }
+  nb_rule<V>(ctx, dir, add);
   const int jn = i + dir;
   if (jn < 0 || jn >= H) return v;
   const float bn = R[sw(base + brev(jn, h))];
   return add ? ((dir > 0) ? (v + bn) : (bn + v)) : (v - bn);
 }
 
-// Two levels of the time-first neighbour relation (M4 / M8 frequency phase,
-// node sizes 2^logLp and 2^(logLp+1)) in one gather pass: each output of the
-// upper level takes the lower level's outputs at its position and at its
-// neighbour's, evaluated from Win on the fly; the same float32 operations as
-// two single-level passes.
+// Two levels of the neighbour relation in one gather pass: node size 2^l1
+// first, then 2^l2 (the time-first variants 4 / 8 climb, l2 = l1 + 1, in the
+// frequency phase; the harmonics-first 2 / 6 descend, l2 = l1 - 1, in the
+// time phase).  Each output of the second level takes the first level's
+// outputs at its position and at its neighbour's, evaluated from Win on the
+// fly: the same float32 operations as two single-level passes.
 template <int V>
-__global__ void mp_neighbour2_kernel(MpArgs a, const float* __restrict__ Win, float* __restrict__ Wout, int logLp) {
-  static_assert(Var<V>::ot && !Var<V>::scan, "the time-first neighbour form");
-  const int half = 1 << (a.logN - 1), l2 = logLp + 1, L2 = 1 << l2, H2 = L2 >> 1, h2 = l2 - 1;
+__global__ void mp_neighbour2_kernel(MpArgs a, const float* __restrict__ Win, float* __restrict__ Wout, int l1,
+                                     int l2) {
+  static_assert(!Var<V>::scan, "the neighbour form");
+  const int half = 1 << (a.logN - 1), L2 = 1 << l2, H2 = L2 >> 1, h2 = l2 - 1;
   const long long total = a.RSg * 4 * mp_nt(a);
   for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
     const long long rr = w / a.RSg;
@@ -263,7 +272,7 @@ __global__ void mp_neighbour2_kernel(MpArgs a, const float* __restrict__ Win, fl
     const int p = sw(ph);
     CRegP R = creg_ptr(Win + rr * a.RSg, (int)a.RSg);
     const int ctx0 = (int)(rr & 1);
-    float v = nb_at<V>(R, p, logLp, half, ctx0);
+    float v = nb_at<V>(R, p, l1, half, ctx0);
     if (p < half - L2) {
       const int p0 = p & ~(L2 - 1);
       const int ctx = node_ctx<V>(p0, l2, half, ctx0);
@@ -272,11 +281,10 @@ __global__ void mp_neighbour2_kernel(MpArgs a, const float* __restrict__ Win, fl
         const int i = brev(p - base, h2);
         int dir;
         bool add;
-        if constexpr (V == 4) { dir = ctx == 0 ? +1 : -1; add = true; }
-        else { dir = ctx == 0 ? -1 : +1; add = false; }  // V == 8
+        nb_rule<V>(ctx, dir, add);
         const int jn = i + dir;
         if (jn >= 0 && jn < H2) {
-          const float bn = nb_at<V>(R, base + brev(jn, h2), logLp, half, ctx0);
+          const float bn = nb_at<V>(R, base + brev(jn, h2), l1, half, ctx0);
           v = add ? ((dir > 0) ? (v + bn) : (bn + v)) : (v - bn);
         }
       }
@@ -548,6 +556,75 @@ __global__ void mp_chain2_kernel(MpArgs a, const float* __restrict__ Win, float*
   }
 }
 
+// The harmonics-first chain (the D_k time phase, descending): level M's
+// output at P + rel from its input R (rel inside its range), and two levels
+// (M, then M/2) in one gather pass.  Level M/2 rewrites exactly level M's te
+// part, so each of its outputs evaluates the two level-M values it needs
+// from Win on the fly; level M's to part is written from its own formula.
+__device__ __forceinline__ float chain_to_value(CRegP R, int ctx0, int P, int Q, int logQ, int M, int rel) {
+  if (ctx0 == 0) {
+    if (rel < Q) {
+      const int n = brev(rel, logQ);
+      return R[sw(P + n)] - R[sw(P + M / 2 - n)];
+    }
+    const int n = rel - Q;
+    return n < Q ? (R[sw(P + n)] + R[sw(P + M / 2 - n)]) : R[sw(P + Q)];
+  }
+  if (rel < Q) {
+    const int n = brev(rel, logQ) + 1;
+    return n < Q ? (R[sw(P + n - 1)] + R[sw(P + M / 2 - n - 1)]) : R[sw(P + Q - 1)];
+  }
+  const int n = rel - Q + 1;
+  return R[sw(P + n - 1)] - R[sw(P + M / 2 - n - 1)];
+}
+
+template <int V>
+__global__ void mp_chain2_to_kernel(MpArgs a, const float* __restrict__ Win, float* __restrict__ Wout, int logM) {
+  static_assert(!Var<V>::ot, "the harmonics-first chain");
+  const int half = 1 << (a.logN - 1);
+  const int M = 1 << logM, logQ = logM - 2, Q = 1 << logQ, P = half - M / 2;  // level M
+  const int M1 = M / 2, logQ1 = logQ - 1, Q1 = Q / 2, P1 = P + Q;            // level M/2
+  const long long total = a.RSg * 4 * mp_nt(a);
+  for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
+    const long long rr = w / a.RSg;
+    const int ph = (int)(w - rr * a.RSg);
+    const int p = sw(ph);
+    CRegP R = creg_ptr(Win + rr * a.RSg, (int)a.RSg);
+    const int ctx0 = (int)(rr & 1);
+    float v = R[ph];
+    const int rel = p - P;
+    const bool inM = ctx0 == 0 ? (rel >= 0 && rel <= M / 2) : (rel >= 0 && rel < M / 2 - 1);
+    if (inM) {
+      if (rel < Q) {
+        v = chain_to_value(R, ctx0, P, Q, logQ, M, rel);  // level M's to part
+      } else {
+        // level M/2 at P1 + r1, its input x at P1 + j being level M's output at rel Q + j
+        auto in1 = [&](int j) { return chain_to_value(R, ctx0, P, Q, logQ, M, Q + j); };
+        const int r1 = rel - Q;
+        if (ctx0 == 0) {
+          if (r1 < Q1) {
+            const int n = brev(r1, logQ1);
+            v = in1(n) - in1(M1 / 2 - n);
+          } else {
+            const int n = r1 - Q1;
+            v = n < Q1 ? (in1(n) + in1(M1 / 2 - n)) : in1(Q1);
+          }
+        } else {
+          if (r1 < Q1) {
+            const int n = brev(r1, logQ1) + 1;
+            v = n < Q1 ? (in1(n - 1) + in1(M1 / 2 - n - 1)) : in1(Q1 - 1);
+          } else {
+            const int n = r1 - Q1 + 1;
+            v = in1(n - 1) - in1(M1 / 2 - n - 1);
+          }
+        }
+        (void)P1;
+      }
+    }
+    Wout[rr * a.RSg + ph] = v;
+  }
+}
+
 // Subproblem solve.  Blocks [0, nnode/2) of each region take one tree node of
 // size 2S each (node mode), the last block the region tail (region mode,
 // N' = 4S).  The words are copied verbatim: S and half - 2S are multiples of
@@ -780,7 +857,7 @@ cudaError_t mp_run(const MpArgs& a0, float* W0, float* W1, const SmallConsts& K,
         ++lp;
       }
       for (; lp + 1 <= logN - 2; lp += 2) {
-        mp_neighbour2_kernel<V><<<grid_for(words), threads, 0, st>>>(a, cur, oth, lp);
+        mp_neighbour2_kernel<V><<<grid_for(words), threads, 0, st>>>(a, cur, oth, lp, lp + 1);
         if ((e = launched()) != cudaSuccess) return e;
         float* t = cur; cur = oth; oth = t;
       }
@@ -803,13 +880,35 @@ cudaError_t mp_run(const MpArgs& a0, float* W0, float* W1, const SmallConsts& K,
       float* t = cur; cur = oth; oth = t;
     }
   } else {
-    for (int lm = logN - 1; lm >= MP_LOG_S + 3; --lm) {
+    // chain levels 2^(n-1) .. 2^(S+3), descending, two a pass (a single one
+    // first when their count is odd)
+    int lm = logN - 1;
+    if (((logN - 1) - (MP_LOG_S + 3) + 1) & 1) {
       mp_chain_kernel<V><<<grid_for(words), threads, 0, st>>>(a, cur, oth, lm);
       if ((e = launched()) != cudaSuccess) return e;
       float* t = cur; cur = oth; oth = t;
+      --lm;
     }
-    for (int lp = logN - 2; lp >= MP_LOG_S + 2; --lp)  // 2^(S+1): in the solve
-      if ((e = relation(lp)) != cudaSuccess) return e;
+    for (; lm - 1 >= MP_LOG_S + 3; lm -= 2) {
+      mp_chain2_to_kernel<V><<<grid_for(words), threads, 0, st>>>(a, cur, oth, lm);
+      if ((e = launched()) != cudaSuccess) return e;
+      float* t = cur; cur = oth; oth = t;
+    }
+    int lp = logN - 2;  // down to 2^(S+2); 2^(S+1) is in the solve
+    if constexpr (!Var<V>::scan) {
+      if (lp >= MP_LOG_S + 2 && ((lp - (MP_LOG_S + 2) + 1) & 1)) {
+        if ((e = relation(lp)) != cudaSuccess) return e;
+        --lp;
+      }
+      for (; lp - 1 >= MP_LOG_S + 2; lp -= 2) {
+        mp_neighbour2_kernel<V><<<grid_for(words), threads, 0, st>>>(a, cur, oth, lp, lp - 1);
+        if ((e = launched()) != cudaSuccess) return e;
+        float* t = cur; cur = oth; oth = t;
+      }
+    } else {
+      for (; lp >= MP_LOG_S + 2; --lp)
+        if ((e = relation(lp)) != cudaSuccess) return e;
+    }
     mp_solve_kernel<V, MP_TPB><<<nsolve, MP_TPB, smem, st>>>(a, cur, K);
     if ((e = launched()) != cudaSuccess) return e;
     for (int b = bp.nb - 1; b >= 0; --b)

@@ -205,9 +205,10 @@ def copy_bandwidth(xh, yh, xd, yd, stream, reps=3):
     g_in, g_out, g_both = nbytes / t_in / 1e6, nbytes / t_out / 1e6, nbytes / t_both / 1e6
     # a pinned -> pinned transform moves 8 bytes a point each way; a direction
     # cannot beat its own copy rate, so min(h2d, d2h) / 8 bounds the points a
-    # second (both directions at once is reported beside it)
+    # second; with the two directions overlapped (as the chunked call runs
+    # them) the tighter bound is their rate when both run at once
     return {"h2d_gbs": g_in, "d2h_gbs": g_out, "both_directions_gbs_each": g_both,
-            "bound_gpts": min(g_in, g_out) / 8.0, "bytes_each": nbytes}
+            "bound_gpts": min(g_in, g_out) / 8.0, "bidirectional_bound_gpts": g_both / 8.0, "bytes_each": nbytes}
 
 
 class ClockSampler:
@@ -752,7 +753,10 @@ def main():
                "step": "one forward transform of the batch, pinned host -> pinned host, through amqft_exec_host",
                "copies": copies,
                "frac_of_copy_bound": (args.batch * n * world / (te * 1e-3) / 1e9) / copies["bound_gpts"]
-               if copies.get("bound_gpts") else None}
+               if copies.get("bound_gpts") else None,
+               "frac_of_bidirectional_copy_bound":
+                   (args.batch * n * world / (te * 1e-3) / 1e9) / copies["bidirectional_bound_gpts"]
+                   if copies.get("bidirectional_bound_gpts") else None}
         del xh, yh
 
     # both constants modes' forward kernel time on this workload, after the timed region

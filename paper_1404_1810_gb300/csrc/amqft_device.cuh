@@ -710,9 +710,13 @@ __device__ __forceinline__ void seg_excl_scan(float* tot, float* wsum, int n, in
 // phase of M1/M5 (ot variants; the first element is halved) or the time
 // phase of M3/M7 (to variants; the last element is halved).  Chunks of C
 // consecutive elements are run sequentially by one thread each; the carries
-// between chunks come from a segmented scan of the chunk totals.
-template <int V, int TPB, int MAXI>
+// between chunks come from a segmented scan of the chunk totals.  The
+// chunking follows CTPB threads (<= TPB; the rest stay idle here), so a
+// kernel shape with more threads can give the same bits as one with CTPB;
+// MAXI bounds the chunk length.
+template <int V, int TPB, int MAXI, int CTPB = TPB>
 __device__ __forceinline__ void pass_recurrence(float* sm, float* tot, float* wsum, const Geo& g, int logLp) {
+  static_assert(CTPB <= TPB, "the chunking's threads");
   constexpr bool hstart = Var<V>::ot;
   constexpr bool alt = (V == 1 || V == 3);
   const int Lp = 1 << logLp, H = Lp >> 1, h = logLp - 1;
@@ -720,7 +724,7 @@ __device__ __forceinline__ void pass_recurrence(float* sm, float* tot, float* ws
   const unsigned total = nb * (unsigned)H * (unsigned)g.nreg;
   const unsigned total_cap = nb * (unsigned)H * (unsigned)g.nreg_cap;
   int logC = 1;
-  while (((unsigned)TPB << logC) < total_cap) ++logC;
+  while (((unsigned)CTPB << logC) < total_cap) ++logC;
   const int C = 1 << logC, logSC = h - logC, SC = 1 << logSC;
   const unsigned nch = total >> logC;
   const Div dv(nb);

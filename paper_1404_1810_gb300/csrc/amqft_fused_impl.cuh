@@ -877,6 +877,10 @@ __device__ __forceinline__ void fused_compute(float* sm, const Geo& g, const Tab
   (void)cctx;
   const int logTop = logN - 2;  // log2 of the largest tree (N/4)
   const BandPlan bp = band_plan(logN);
+  // the recurrences' scan chunking of the single-CTA path follows its
+  // 256-thread shape in every launch shape (a transform's bits never depend on
+  // the shape that ran it)
+  constexpr int RC_TPB = CL == 1 ? SMALL_TPB : TPB, RC_MAXI = CL == 1 ? SMALL_MAXI : MAXI;
   if constexpr (Var<V>::ot) {
 #pragma unroll
     for (int b = 0; b < bp.nb; ++b) {
@@ -901,7 +905,7 @@ __device__ __forceinline__ void fused_compute(float* sm, const Geo& g, const Tab
     }
     if constexpr (Var<V>::scan) {
       for (int lp = LOG_LEAF + 1; lp <= logTop; ++lp) {
-        pass_recurrence<V, TPB, MAXI>(sm, tot, wsum, g, lp);
+        pass_recurrence<V, TPB, RC_MAXI, RC_TPB>(sm, tot, wsum, g, lp);
         __syncthreads();
       }
     } else {
@@ -937,7 +941,7 @@ __device__ __forceinline__ void fused_compute(float* sm, const Geo& g, const Tab
     for (int r = threadIdx.x; r < g.nreg; r += TPB) run_tail<V>(reg_ptr(sm + r * g.RS, g.RS), ctx_of(g, r), logN, K);
     __syncthreads();
     for (int lp = logTop; lp >= LOG_LEAF + 1; --lp) {
-      if constexpr (Var<V>::scan) pass_recurrence<V, TPB, MAXI>(sm, tot, wsum, g, lp);
+      if constexpr (Var<V>::scan) pass_recurrence<V, TPB, RC_MAXI, RC_TPB>(sm, tot, wsum, g, lp);
       else pass_neighbour<V, TPB, MAXI>(sm, g, lp);
       __syncthreads();
     }
@@ -1210,15 +1214,12 @@ cudaError_t launch_v(const FusedArgs& a, const SmallConsts& K, const FusedConfig
   if (c.cluster == 1) {
     const long long grid = (a.batch + c.per_cta - 1) / c.per_cta;
     // A call that fills one CTA at most is latency-bound: 512 threads (half
-    // the items per thread in every pass), one CTA per SM.  Only for the
-    // variants without recurrences, whose results do not depend on the
-    // thread count (the recurrences' scan chunking does), so a transform's
-    // bits never depend on its batch.
-    if constexpr (!Var<V>::scan) {
-      if (grid == 1)
-        return launch_cfg<V, 2 * SMALL_TPB, SMALL_MAXI / 2, 1, 0>(a, K, grid, c.smem + SMALL_TPB * (int)sizeof(float),
-                                                                  st);
-    }
+    // the items per thread in every pass), one CTA per SM.  The recurrences
+    // keep the 256-thread scan chunking, so the results are those of the
+    // 256-thread shape and a transform's bits never depend on its batch.
+    if (grid == 1)
+      return launch_cfg<V, 2 * SMALL_TPB, SMALL_MAXI / 2, 1, 0>(a, K, grid, c.smem + SMALL_TPB * (int)sizeof(float),
+                                                                st);
     return launch_cfg<V, SMALL_TPB, SMALL_MAXI, 1, 0>(a, K, grid, c.smem, st);
   }
   switch (a.logN) {

@@ -74,10 +74,13 @@ static cudaError_t ragged_launch(int variant, const FusedArgs& a, const SmallCon
 }
 
 // Bucket pass of a ragged batch: transform ids into one list per log2 N.
+// ubase > 0: a transform of 2^14..2^16 whose data is not 16-byte aligned
+// (offset + par odd, par = the parity of the base pointers in 8-byte words)
+// goes to class ubase + (log2 N - 14) instead of its length's
 __global__ void ragged_bucket_kernel(const unsigned char* __restrict__ log2n, const long long* __restrict__ off,
                                      long long count, int maxlog, long long max_points, int* cnt, int* list,
                                      long long cap, int* skipped, const float2* __restrict__ in,
-                                     float2* __restrict__ out) {
+                                     float2* __restrict__ out, int ubase, int par) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < count;
        i += (long long)gridDim.x * blockDim.x) {
     const int c = log2n[i];
@@ -89,14 +92,15 @@ __global__ void ragged_bucket_kernel(const unsigned char* __restrict__ log2n, co
       out[off[i]] = in[off[i]];
       continue;
     }
-    const int pos = atomicAdd(cnt + c, 1);
+    const int cls = ubase > 0 && c >= 14 && c <= 16 && ((off[i] + par) & 1) ? ubase + (c - 14) : c;
+    const int pos = atomicAdd(cnt + cls, 1);
     // multi-pass lengths: the workspace holds max_points >> c transforms
     const long long capc = c > AMQFT_LOG2N_FUSED_MAX && (max_points >> c) < cap ? (max_points >> c) : cap;
     if (pos >= capc) {
       atomicAdd(skipped, 1);
       continue;
     }
-    list[c * cap + pos] = (int)i;
+    list[cls * cap + pos] = (int)i;
   }
 }
 
@@ -730,6 +734,14 @@ static long long ragged_capacity(const amqft_plan_s* p, int c) {
 
 static long long region_stride_g(int c) { return (((1LL << (c - 1)) + 2 + 31) / 32) * 32; }
 
+// class index of the unaligned 2^14 list of a ragged call (0: no split, every
+// 2^14..2^16 transform on the fused cluster kernels): the paired-region
+// kernel runs variant 4, and needs in and out at the same 16-byte phase
+static int ragged_ubase(amqft_plan_t p, const void* in, const void* out) {
+  const bool same = (((uintptr_t)in ^ (uintptr_t)out) & 8u) == 0;
+  return p->variant == 4 && p->log2n >= 14 && same ? p->log2n + 1 : 0;
+}
+
 int amqft_plan_ragged(amqft_plan_t* out, int max_log2n, int variant, int dtype, int64_t max_count,
                       int64_t max_points) {
   t_err.clear();
@@ -746,7 +758,8 @@ int amqft_plan_ragged(amqft_plan_t* out, int max_log2n, int variant, int dtype, 
   p->max_count = max_count;
   p->max_points = max_points;
   cudaError_t e = cudaMalloc(&p->d_rcnt, 64 * sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&p->d_rlist, (size_t)(max_log2n + 1) * (size_t)max_count * sizeof(int));
+  // one list per length, and three for the unaligned transforms of 2^14..2^16
+  if (e == cudaSuccess) e = cudaMalloc(&p->d_rlist, (size_t)(max_log2n + 4) * (size_t)max_count * sizeof(int));
   long long ws = 0;
   for (int c = AMQFT_LOG2N_FUSED_MAX + 1; c <= max_log2n; ++c) {
     const long long need = 2LL * ragged_capacity(p, c) * 4 * region_stride_g(c);
@@ -782,7 +795,8 @@ int amqft_exec_ragged(amqft_plan_t p, int64_t count, const int64_t* d_offsets, c
     if (blocks > 8LL * p->num_sms) blocks = 8LL * p->num_sms;
     ragged_bucket_kernel<<<(unsigned)blocks, 256, 0, st>>>(d_log2n, (const long long*)d_offsets, count, p->log2n,
                                                            p->max_points, p->d_rcnt, p->d_rlist, p->max_count,
-                                                           p->d_rcnt + 33, (const float2*)in, (float2*)out);
+                                                           p->d_rcnt + 33, (const float2*)in, (float2*)out,
+                                                           ragged_ubase(p, in, out), (int)(((uintptr_t)in >> 3) & 1));
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "ragged bucket launch");
     ++p->launches;
   }
@@ -800,6 +814,7 @@ int amqft_exec_ragged(amqft_plan_t p, int64_t count, const int64_t* d_offsets, c
   r.cap = p->max_count;
   r.work = p->d_rcnt + 32;
   r.maxlog = p->log2n < AMQFT_LOG2N_FUSED_MAX ? p->log2n : AMQFT_LOG2N_FUSED_MAX;
+  r.ubase = ragged_ubase(p, in, out);
   r.sched = p->knob[0];
   r.order = p->knob[1];
   RaggedLaunch L;

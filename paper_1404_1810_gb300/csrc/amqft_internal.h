@@ -88,14 +88,18 @@ AMQFT_BOUNDS_DECL(bounds_p16)
 // storage, batch below 2^31): one transform per cluster of four CTAs,
 // persistent over the batch; in and out 16-byte (16-bit: 8-byte) aligned
 bool paired_supported(int logN, int variant, int dtype, long long batch);
+// tlist / toff / tcount (all NULL: transforms 0 .. batch-1 in order): the
+// ragged form, list entries t < min(*tcount, batch) at element toff[tlist[t]]
+// (each 16-byte aligned)
 cudaError_t paired_launch(int logN, const void* in, void* out, const int* exp_in, int* exp_out, int dtype,
-                          long long batch, int inverse, const float* ctab, const SmallConsts& K, cudaStream_t st);
+                          long long batch, int inverse, const float* ctab, const SmallConsts& K, cudaStream_t st,
+                          const int* tlist = nullptr, const long long* toff = nullptr, const int* tcount = nullptr);
 cudaError_t paired_launch_14(const void*, void*, const int*, int*, int, long long, int, const float*, const SmallConsts&,
-                             cudaStream_t);
+                             cudaStream_t, const int*, const long long*, const int*);
 cudaError_t paired_launch_15(const void*, void*, const int*, int*, int, long long, int, const float*, const SmallConsts&,
-                             cudaStream_t);
+                             cudaStream_t, const int*, const long long*, const int*);
 cudaError_t paired_launch_16(const void*, void*, const int*, int*, int, long long, int, const float*, const SmallConsts&,
-                             cudaStream_t);
+                             cudaStream_t, const int*, const long long*, const int*);
 
 // Read-only view of a plan, for entry points defined outside the plan's
 // translation unit.  Returns AMQFT_ERR_ARG for a NULL plan.

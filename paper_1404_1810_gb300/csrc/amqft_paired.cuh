@@ -758,6 +758,16 @@ struct Store16 {
   int dtype;          // 1 bf16, 2 fp16, 3 int16
 };
 
+// Which transforms the cluster runs: t = 0 .. batch-1 at element t * N, or
+// (a ragged batch) list entries t < min(*count, batch) at element
+// offset[list[t]], each 16-byte aligned, the count written by an earlier
+// kernel of the stream.
+struct TList {
+  const int* list;
+  const long long* offset;
+  const int* count;
+};
+
 PR_HD float f32_from_bits(uint32_t u) {
 #if defined(__CUDA_ARCH__)
   return __uint_as_float(u);
@@ -1024,7 +1034,8 @@ PR_HD void store_stage(Ctx& cx, void* xo, int r, const Store16* io, long long t)
 // (float2 index into the region: distributed shared memory for the others).
 template <int LN, bool INV, bool H, class Ctx>
 PR_HD void paired_body(Ctx& cx, const void* in, void* out, const Store16* io, int batch, int cid, int ncl,
-                       float2* reg, float* __restrict__ cst, const float* __restrict__ ctab, const LeafConsts& K) {
+                       float2* reg, float* __restrict__ cst, const float* __restrict__ ctab, const LeafConsts& K,
+                       const TList& tl = TList{nullptr, nullptr, nullptr}) {
   constexpr int T = LN - 2, NT = 1 << (T - 5);
   constexpr long long N = 1LL << LN;
   constexpr int ES = H ? 4 : 8;  // bytes per element in HBM
@@ -1033,8 +1044,10 @@ PR_HD void paired_body(Ctx& cx, const void* in, void* out, const Store16* io, in
   if (ctab)  // else the kernel has evaluated them on the fly
     for (int i = tid; i < ncst; i += NT) cst[i] = ctab[30 + i];
   const int dt = H ? io->dtype : 0;
+  if (tl.count && *tl.count < batch) batch = *tl.count;
   auto at = [&](const void* base, long long t) {
-    return static_cast<const void*>(static_cast<const char*>(base) + t * N * ES);
+    const long long e = tl.list ? tl.offset[tl.list[t]] : t * N;
+    return static_cast<const void*>(static_cast<const char*>(base) + e * ES);
   };
   // 2^exp_in of transform t (16-bit input)
   auto scale = [&](long long t) { return H && io->exp_in ? pow2_exact(io->exp_in[t]) : 1.f; };

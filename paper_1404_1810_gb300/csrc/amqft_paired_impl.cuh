@@ -154,8 +154,8 @@ __host__ __device__ constexpr int paired_ctas(int LN) { return LN >= 16 ? 1 : (L
 
 template <int LN, bool INV, bool H>
 __global__ void __launch_bounds__(paired_tpb(LN), paired_ctas(LN))
-    paired_kernel(const void* __restrict__ in, void* __restrict__ out, const Store16 io, long long batch,
-                  const float* __restrict__ ctab, const __grid_constant__ LeafConsts K) {
+    paired_kernel(const void* __restrict__ in, void* __restrict__ out, const Store16 io, const TList tl,
+                  long long batch, const float* __restrict__ ctab, const __grid_constant__ LeafConsts K) {
   constexpr int T = LN - 2;
   extern __shared__ __align__(16) float2 psm[];
   cg::cluster_group cl = cg::this_cluster();
@@ -168,7 +168,7 @@ __global__ void __launch_bounds__(paired_tpb(LN), paired_ctas(LN))
   cx.es = H ? 4 : 8;
   cx.gin = static_cast<const char*>(in);
   cx.gout = static_cast<const char*>(out);
-  cx.gn = batch << LN;
+  cx.gn = tl.list ? (1LL << 62) / cx.es : batch << LN;  // a ragged buffer's extent is the caller's
 #endif
   float* cst = reinterpret_cast<float*>(psm + region_f2<T>());
   if (!ctab) {  // constants on the fly: the same entries paired_body copies from the table
@@ -176,12 +176,12 @@ __global__ void __launch_bounds__(paired_tpb(LN), paired_ctas(LN))
     for (int i = cx.tid; i < ncst; i += paired_tpb(LN)) cst[i] = fly_entry<4>(30 + i);
   }
   paired_body<LN, INV, H>(cx, in, out, &io, (int)batch, (int)(blockIdx.x >> 2), (int)(gridDim.x >> 2), psm, cst,
-                          ctab, K);
+                          ctab, K, tl);
 }
 
 template <int LN, bool INV, bool H>
-static cudaError_t launch(const void* in, void* out, const Store16& io, long long batch, const float* ctab,
-                          const LeafConsts& K, cudaStream_t st) {
+static cudaError_t launch(const void* in, void* out, const Store16& io, const TList& tl, long long batch,
+                          const float* ctab, const LeafConsts& K, cudaStream_t st) {
   constexpr int T = LN - 2, SMEM = smem_bytes<T>();
   auto kern = paired_kernel<LN, INV, H>;
   // the number of clusters that fit on the device at once, queried once
@@ -209,23 +209,25 @@ static cudaError_t launch(const void* in, void* out, const Store16& io, long lon
   }
   const long long ncl = batch < max_clusters[INV] ? batch : max_clusters[INV];
   cfg.gridDim = dim3((unsigned)(4 * ncl), 1, 1);
-  return cudaLaunchKernelEx(&cfg, kern, in, out, io, batch, ctab, K);
+  return cudaLaunchKernelEx(&cfg, kern, in, out, io, tl, batch, ctab, K);
 }
 
 
 template <int LN>
 cudaError_t launch_len(const void* in, void* out, const int* exp_in, int* exp_out, int dtype, long long batch,
-                       int inverse, const float* ctab, const SmallConsts& K, cudaStream_t st) {
+                       int inverse, const float* ctab, const SmallConsts& K, cudaStream_t st, const int* tlist,
+                       const long long* toff, const int* tcount) {
   LeafConsts L;
   for (int i = 0; i < 30; ++i) L.c[i] = K.c[i];
   L.cos_pi4 = K.cos_pi4;
   L.nz = -0.0f;
   const Store16 io{exp_in, exp_out, dtype};
+  const TList tl{tlist, toff, tcount};
   if (dtype == 0)
-    return inverse ? launch<LN, true, false>(in, out, io, batch, ctab, L, st)
-                   : launch<LN, false, false>(in, out, io, batch, ctab, L, st);
-  return inverse ? launch<LN, true, true>(in, out, io, batch, ctab, L, st)
-                 : launch<LN, false, true>(in, out, io, batch, ctab, L, st);
+    return inverse ? launch<LN, true, false>(in, out, io, tl, batch, ctab, L, st)
+                   : launch<LN, false, false>(in, out, io, tl, batch, ctab, L, st);
+  return inverse ? launch<LN, true, true>(in, out, io, tl, batch, ctab, L, st)
+                 : launch<LN, false, true>(in, out, io, tl, batch, ctab, L, st);
 }
 
 }  // namespace pr

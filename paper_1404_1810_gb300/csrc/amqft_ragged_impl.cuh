@@ -27,6 +27,9 @@ struct RaggedArgs {
   int maxlog;         // largest log2 N of the plan
   int sched;          // 0: static round robin, 1: dynamic (atomic counter)
   int order;          // 0: longest lengths first, 1: shortest first
+  int ubase;          // > 0: the transforms of 2^14..2^16 whose offset is not
+                      // 16-byte aligned are listed apart, as classes ubase + 0..2
+                      // (the others run on the paired-region kernel)
 };
 
 __host__ __device__ constexpr int small_tot_off(int logN) {
@@ -84,18 +87,18 @@ __global__ void __launch_bounds__(SMALL_TPB, 2) ragged_small_kernel(const FusedA
 
 template <int V, int LN, int TPB = cluster_tpb(LN, Var<V>::ot)>
 __global__ void __launch_bounds__(TPB, ctas_per_sm(TPB)) ragged_cluster_kernel(const FusedArgs a0, const __grid_constant__ SmallConsts K,
-                                                             const RaggedArgs r) {
+                                                             const RaggedArgs r, int cls) {
   extern __shared__ __align__(16) float sm[];
-  const int n = r.cnt[LN];
+  const int n = r.cnt[cls];
   const int ncl = (int)(gridDim.x / 4);
   for (int j = (int)(blockIdx.x / 4); j < n; j += ncl)
-    fused_body<V, TPB, cluster_maxi(LN, Var<V>::ot), 4, LN>(a0, K, sm, j, 1, LN, 0, a0.tot_off, r.list + LN * r.cap);
+    fused_body<V, TPB, cluster_maxi(LN, Var<V>::ot), 4, LN>(a0, K, sm, j, 1, LN, 0, a0.tot_off, r.list + cls * r.cap);
 }
 
 // host: launch one persistent cluster grid for length 2^LN
 template <int V, int LN>
 cudaError_t ragged_cluster_launch(const FusedArgs& a, const SmallConsts& K, const RaggedArgs& r, int clusters,
-                                  int smem, cudaStream_t st) {
+                                  int smem, cudaStream_t st, int cls = LN) {
   constexpr int TPB = cluster_tpb(LN, Var<V>::ot);
   auto kern = ragged_cluster_kernel<V, LN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -112,7 +115,7 @@ cudaError_t ragged_cluster_launch(const FusedArgs& a, const SmallConsts& K, cons
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, kern, a, K, r);
+  return cudaLaunchKernelEx(&cfg, kern, a, K, r, cls);
 }
 
 // Launch geometry chosen by the host (and the autotuner).
@@ -138,6 +141,24 @@ cudaError_t ragged_run(const FusedArgs& a0, const SmallConsts& K, const RaggedAr
     if (nlaunch) ++*nlaunch;
   }
   FusedArgs a = a0;
+  if (V == 4 && r.ubase > 0) {
+    // 2^14 .. 2^16: the paired-region kernel over each length's aligned list,
+    // the fused cluster kernel over the transforms listed apart
+    for (int q = 0; q < 3 && 14 + q <= r.maxlog; ++q) {
+      const int c = 14 + q;
+      e = paired_launch(c, a0.in, a0.out, nullptr, nullptr, 0, r.cap, a0.inverse, a0.ctab, K, st, r.list + c * r.cap,
+                        a0.toff, r.cnt + c);
+      if (e != cudaSuccess) return e;
+      if (nlaunch) ++*nlaunch;
+      a.tot_off = L.cluster_tot_off[q];
+      if (q == 0) e = ragged_cluster_launch<V, 14>(a, K, r, L.clusters[0], L.cluster_smem[0], st, r.ubase);
+      else if (q == 1) e = ragged_cluster_launch<V, 15>(a, K, r, L.clusters[1], L.cluster_smem[1], st, r.ubase + 1);
+      else e = ragged_cluster_launch<V, 16>(a, K, r, L.clusters[2], L.cluster_smem[2], st, r.ubase + 2);
+      if (e != cudaSuccess) return e;
+      if (nlaunch) ++*nlaunch;
+    }
+    return cudaSuccess;
+  }
   if (r.maxlog >= 14) {
     a.tot_off = L.cluster_tot_off[0];
     e = ragged_cluster_launch<V, 14>(a, K, r, L.clusters[0], L.cluster_smem[0], st);

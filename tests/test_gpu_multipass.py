@@ -249,8 +249,9 @@ def test_launch_count():
     p.fwd(x16)
     assert p.launches() == _mp_launches(17, dtype16=True)
     p.close()
-    # ragged: bucket, the persistent small launch, three cluster launches and
-    # the multi-pass sequences of 2^17 and 2^18
+    # ragged: bucket, the persistent small launch, for each of 2^14..2^16 the
+    # paired-region launch (aligned transforms) and a cluster launch (the
+    # others), and the multi-pass sequences of 2^17 and 2^18
     lg = torch.tensor([4, 10, 14, 15, 16, 17, 18], dtype=torch.uint8, device="cuda")
     n = (1 << lg.to(torch.int64))
     off = torch.cumsum(n, 0) - n
@@ -258,5 +259,5 @@ def test_launch_count():
     rp = RaggedPlan(18, 4, 16, 1 << 20)
     rp.exec(x, lg, off)
     torch.cuda.synchronize()
-    assert rp.launches() == 1 + 1 + 3 + _mp_launches(17) + _mp_launches(18)
+    assert rp.launches() == 1 + 1 + 6 + _mp_launches(17) + _mp_launches(18)
     rp.close()

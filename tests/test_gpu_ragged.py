@@ -208,3 +208,40 @@ def test_autotuner_picks_a_valid_setting(tmp_path):
         assert torch.equal(y, batched_reference(x, lg, off, 4, False))
     finally:
         p.close()
+
+
+@pytest.mark.parametrize("shift", [0, 1])
+def test_ragged_unaligned_offsets(shift):
+    """Variant 4 runs the 2^14..2^16 transforms of a ragged batch on the
+    paired-region kernel when their data is 16-byte aligned and on the fused
+    cluster kernel otherwise (odd element offsets, or in and out at different
+    16-byte phases): every transform still equals the per-length batched call."""
+    import torch
+
+    from paper_1404_1810_gb300 import RaggedPlan
+
+    lg = np.array([14, 15, 16, 14, 16, 15, 3, 14], dtype=np.uint8)
+    n = 1 << lg.astype(np.int64)
+    gaps = np.array([1, 0, 1, 1, 0, 0, 1, 0])               # one-element gaps make odd offsets
+    off = np.cumsum(n + gaps) - n
+    total = int(off[-1] + n[-1]) + 2
+    data = synth.normal_complex(total, 1, config=4, stream=77)[0].astype(np.complex64)
+    base = torch.zeros(total + 2, dtype=torch.complex64, device="cuda")
+    x = base[shift:shift + total]                            # shift 1: the buffer at an odd 8-byte phase
+    x.copy_(torch.from_numpy(data))
+    lgd, offd = torch.from_numpy(lg).cuda(), torch.from_numpy(off.astype(np.int64)).cuda()
+    p = RaggedPlan(16, 4, len(lg), total)
+    try:
+        for inverse in (False, True):
+            for out_shift in (0, 1):
+                ob = torch.zeros(total + 2, dtype=torch.complex64, device="cuda")
+                out = ob[out_shift:out_shift + total]
+                p.exec(x, lgd, offd, out=out, inverse=inverse)
+                torch.cuda.synchronize()
+                assert p.skipped() == 0
+                ref = batched_reference(x, lg, off, 4, inverse)
+                for i in range(len(lg)):
+                    a, b = int(off[i]), int(off[i] + n[i])
+                    assert torch.equal(out[a:b], ref[a:b]), (shift, out_shift, inverse, i)
+    finally:
+        p.close()

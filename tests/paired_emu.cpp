@@ -133,7 +133,7 @@ long double cos_turn(long long num, long long den) {
 }
 
 template <int LN, bool INV, bool H>
-void run(const void* in, void* out, const Store16* io, long long batch) {
+void run(const void* in, void* out, const Store16* io, long long batch, const TList& tl) {
   constexpr int T = LN - 2, NT = 1 << (T - 5), N = 1 << LN;
   std::vector<float> ctab(N / 4 - 2);
   for (long long M = 16; M <= N; M *= 2)
@@ -160,7 +160,7 @@ void run(const void* in, void* out, const Store16* io, long long batch) {
         cx.cred = &red[q * NT];
         cx.nth = NT;
         float* cst = reinterpret_cast<float*>(regs[q] + region_f2<T>());
-        paired_body<LN, INV, H>(cx, in, out, io, (int)batch, 0, 1, regs[q], cst, ctab.data(), K);
+        paired_body<LN, INV, H>(cx, in, out, io, (int)batch, 0, 1, regs[q], cst, ctab.data(), K, tl);
       });
   for (auto& x : th) x.join();
 }
@@ -169,9 +169,13 @@ void run(const void* in, void* out, const Store16* io, long long batch) {
 
 int main(int argc, char** argv) {
   // paired_emu <inverse> <batch> <in.bin> <out.bin> [dtype exp_in.bin exp_out.bin]
+  // a negative batch -b: the b transforms through a transform list, in
+  // reverse order, the count read as the kernel reads it
   if (argc != 5 && argc != 8) return 2;
   const int inv = atoi(argv[1]);
-  const long long batch = atoll(argv[2]);
+  long long batch = atoll(argv[2]);
+  const bool listed = batch < 0;
+  if (listed) batch = -batch;
   const long long N = 1LL << PAIRED_LN;
   const int dt = argc == 8 ? atoi(argv[5]) : 0;
   const size_t es = dt ? 4 : 8;
@@ -186,12 +190,21 @@ int main(int argc, char** argv) {
     fclose(f);
   }
   const Store16 io{ein.data(), eout.data(), dt};
+  std::vector<int> list(batch);
+  std::vector<long long> offs(batch);
+  for (long long t = 0; t < batch; ++t) {
+    list[t] = (int)(batch - 1 - t);
+    offs[t] = t * N;
+  }
+  const int count = (int)batch;
+  const TList tl = listed ? TList{list.data(), offs.data(), &count} : TList{nullptr, nullptr, nullptr};
+  const long long cap = listed ? batch + 3 : batch;  // a list's capacity may exceed its count
   if (dt) {
-    if (inv) run<PAIRED_LN, true, true>(in.data(), out.data(), &io, batch);
-    else run<PAIRED_LN, false, true>(in.data(), out.data(), &io, batch);
+    if (inv) run<PAIRED_LN, true, true>(in.data(), out.data(), &io, cap, tl);
+    else run<PAIRED_LN, false, true>(in.data(), out.data(), &io, cap, tl);
   } else {
-    if (inv) run<PAIRED_LN, true, false>(in.data(), out.data(), nullptr, batch);
-    else run<PAIRED_LN, false, false>(in.data(), out.data(), nullptr, batch);
+    if (inv) run<PAIRED_LN, true, false>(in.data(), out.data(), nullptr, cap, tl);
+    else run<PAIRED_LN, false, false>(in.data(), out.data(), nullptr, cap, tl);
   }
   f = fopen(argv[4], "wb");
   if (!f || fwrite(out.data(), 1, out.size(), f) != out.size()) return 4;

@@ -37,14 +37,14 @@ def emu_binary(tmp_path_factory):
     return build
 
 
-def _run(orc, binary, log2n, batch, inverse, tmp_path):
+def _run(orc, binary, log2n, batch, inverse, tmp_path, listed=False):
     n = 1 << log2n
     x = synth.normal_complex(n, batch, config=2, stream=700 + log2n).astype(np.complex64)
     fi, fo = str(tmp_path / "in.bin"), str(tmp_path / "out.bin")
     x.tofile(fi)
     env = dict(os.environ, ASAN_OPTIONS="detect_leaks=0:detect_stack_use_after_return=0")
-    r = subprocess.run([binary, str(int(inverse)), str(batch), fi, fo], capture_output=True, text=True, env=env,
-                       timeout=900)
+    r = subprocess.run([binary, str(int(inverse)), str(-batch if listed else batch), fi, fo], capture_output=True,
+                       text=True, env=env, timeout=900)
     assert r.returncode == 0, r.stderr[-2000:]
     y = np.fromfile(fo, dtype=np.complex64).reshape(batch, n)
     sign = +1 if inverse else -1
@@ -104,3 +104,9 @@ def _run16(orc, binary, log2n, batch, dt, tmp_path):
 @pytest.mark.parametrize("dt", [1, 3])
 def test_paired_emulation_16bit(orc, emu_binary, dt, tmp_path):
     _run16(orc, emu_binary(14), 14, 2, dt, tmp_path)
+
+
+def test_paired_emulation_transform_list(orc, emu_binary, tmp_path):
+    """The ragged form: transforms taken through a list (reversed order,
+    a capacity above the count read from device memory)."""
+    _run(orc, emu_binary(14), 14, 3, False, tmp_path, listed=True)

@@ -1,4 +1,4 @@
-// Multi-pass AM-QFT for 2^17 <= N <= 2^24: the same recursion and the same
+// Multi-pass AM-QFT for 2^17 <= N <= 2^28: the same recursion and the same
 // float32 operations as the fused kernel, with the four regions of each
 // transform held in a global workspace (same chain layout and swizzle).
 //
@@ -6,11 +6,11 @@
 //            scattered into the regions;
 //   levels   tree levels of node size > S in bands of up to four levels per
 //            pass (the fused kernel's fold and chunk bands, in place in the
-//            workspace), the M2/M4/M6/M8 neighbour phase one level per pass in
-//            gather form, the M1/M3/M5/M7 recurrences one level per three
-//            passes (chunk totals, a scan of the totals per node, the chunks
-//            re-run with their carries), and chain levels of periodisation
-//            > 4S one per pass;
+//            workspace), the M2/M4/M6/M8 neighbour phase of node sizes above
+//            2S two levels per gather pass, the M1/M3/M5/M7 recurrences one
+//            level per three passes (chunk totals, a scan of the totals per
+//            node, the chunks re-run with their carries), and chain levels of
+//            periodisation > 4S two per gather pass;
 //   solve    one CTA per tree node of size 2S (node mode: its two children of
 //            size S and its own M_v relation) and one per region tail (the
 //            trees of size <= S plus the chain up to 4S, a region of N' = 4S)

@@ -193,9 +193,11 @@ template <int V>
 __global__ void mp_neighbour_kernel(MpArgs a, const float* __restrict__ Win, float* __restrict__ Wout, int logLp) {
   const int half = 1 << (a.logN - 1), Lp = 1 << logLp, H = Lp >> 1, h = logLp - 1;
   const long long total = a.RSg * 4 * mp_nt(a);
+  const Div dvr((unsigned)a.RSg);  // total < 2^32 (checked by the host)
   for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
-    const long long rr = w / a.RSg;
-    const int ph = (int)(w - rr * a.RSg);  // physical (swizzled) word
+    const unsigned rq = dvr((unsigned)w);
+    const long long rr = rq;
+    const int ph = (int)((unsigned)w - rq * (unsigned)a.RSg);  // physical (swizzled) word
     const int p = sw(ph);                  // logical position (sw is an involution)
     CRegP R = creg_ptr(Win + rr * a.RSg, (int)a.RSg);
     float v = R[ph];
@@ -266,9 +268,11 @@ __global__ void mp_neighbour2_kernel(MpArgs a, const float* __restrict__ Win, fl
   static_assert(!Var<V>::scan, "the neighbour form");
   const int half = 1 << (a.logN - 1), L2 = 1 << l2, H2 = L2 >> 1, h2 = l2 - 1;
   const long long total = a.RSg * 4 * mp_nt(a);
+  const Div dvr((unsigned)a.RSg);  // total < 2^32 (checked by the host)
   for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
-    const long long rr = w / a.RSg;
-    const int ph = (int)(w - rr * a.RSg);
+    const unsigned rq = dvr((unsigned)w);
+    const long long rr = rq;
+    const int ph = (int)((unsigned)w - rq * (unsigned)a.RSg);
     const int p = sw(ph);
     CRegP R = creg_ptr(Win + rr * a.RSg, (int)a.RSg);
     const int ctx0 = (int)(rr & 1);
@@ -446,9 +450,11 @@ template <int V>
 __global__ void mp_chain_kernel(MpArgs a, const float* __restrict__ Win, float* __restrict__ Wout, int logM) {
   const int half = 1 << (a.logN - 1), M = 1 << logM, logQ = logM - 2, Q = 1 << logQ, P = half - M / 2;
   const long long total = a.RSg * 4 * mp_nt(a);
+  const Div dvr((unsigned)a.RSg);  // total < 2^32 (checked by the host)
   for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
-    const long long rr = w / a.RSg;
-    const int ph = (int)(w - rr * a.RSg);
+    const unsigned rq = dvr((unsigned)w);
+    const long long rr = rq;
+    const int ph = (int)((unsigned)w - rq * (unsigned)a.RSg);
     const int p = sw(ph);
     CRegP R = creg_ptr(Win + rr * a.RSg, (int)a.RSg);
     const int ctx0 = (int)(rr & 1);
@@ -526,9 +532,11 @@ __global__ void mp_chain2_kernel(MpArgs a, const float* __restrict__ Win, float*
   const int M = 1 << logM, logQ = logM - 2, Q = 1 << logQ, P = half - M / 2;          // level M
   const int M2 = 2 * M, logQ2 = logQ + 1, Q2 = 2 * Q, P2 = half - M;                  // level 2M
   const long long total = a.RSg * 4 * mp_nt(a);
+  const Div dvr((unsigned)a.RSg);  // total < 2^32 (checked by the host)
   for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
-    const long long rr = w / a.RSg;
-    const int ph = (int)(w - rr * a.RSg);
+    const unsigned rq = dvr((unsigned)w);
+    const long long rr = rq;
+    const int ph = (int)((unsigned)w - rq * (unsigned)a.RSg);
     const int p = sw(ph);
     CRegP R = creg_ptr(Win + rr * a.RSg, (int)a.RSg);
     const int ctx0 = (int)(rr & 1);
@@ -585,9 +593,11 @@ __global__ void mp_chain2_to_kernel(MpArgs a, const float* __restrict__ Win, flo
   const int M = 1 << logM, logQ = logM - 2, Q = 1 << logQ, P = half - M / 2;  // level M
   const int M1 = M / 2, logQ1 = logQ - 1, Q1 = Q / 2, P1 = P + Q;            // level M/2
   const long long total = a.RSg * 4 * mp_nt(a);
+  const Div dvr((unsigned)a.RSg);  // total < 2^32 (checked by the host)
   for (long long w = (long long)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (long long)gridDim.x * blockDim.x) {
-    const long long rr = w / a.RSg;
-    const int ph = (int)(w - rr * a.RSg);
+    const unsigned rq = dvr((unsigned)w);
+    const long long rr = rq;
+    const int ph = (int)((unsigned)w - rq * (unsigned)a.RSg);
     const int p = sw(ph);
     CRegP R = creg_ptr(Win + rr * a.RSg, (int)a.RSg);
     const int ctx0 = (int)(rr & 1);
@@ -800,6 +810,7 @@ cudaError_t mp_run(const MpArgs& a0, float* W0, float* W1, const SmallConsts& K,
   float* cur = W0;
   float* oth = W1;
   const long long words = a.RSg * 4 * a.nt;
+  if (words >= (1LL << 32)) return cudaErrorInvalidValue;  // the gather passes index words in 32 bits
   mp_load_kernel<V><<<grid_for(a.nt * (N / 4)), threads, 0, st>>>(a, cur);
   if ((e = launched()) != cudaSuccess) return e;
   const int smem = mp_solve_smem_bytes();

@@ -130,3 +130,49 @@ def test_autograd_plan_cache_is_bounded(monkeypatch):
         assert autograd.plan_for(10, 4, 1, 0) is first
     finally:
         autograd._plans.clear()
+
+
+def _umulhi(a, b):
+    return (int(a) * int(b)) >> 32
+
+
+def _div_model(n, d):
+    """The kernels' Div helper: a multiply-high by ceil(2^32 / d) and one
+    correction step, all in 32-bit unsigned arithmetic."""
+    m = (0xFFFFFFFF // d + 1) & 0xFFFFFFFF if d > 1 else 0
+    q = _umulhi(n, m) if d > 1 else n
+    r = (n - q * d) & 0xFFFFFFFF
+    r = r - (1 << 32) if r >= 1 << 31 else r
+    if r < 0:
+        q -= 1
+    elif r >= d:
+        q += 1
+    return q
+
+
+def test_multipass_word_index_fits_32_bits():
+    """The multi-pass gather passes split a word index w into (region,
+    word) with the 32-bit Div helper, valid while a chunk's words stay below
+    2^32.  The plan sizes chunks to a 2 GiB workspace of two buffers of four
+    regions per transform (one transform's buffers if larger); check the
+    bound at every multi-pass length and the split at the region edges."""
+    import re
+
+    src = open(os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))),
+                            "paper_1404_1810_gb300", "csrc", "amqft_api.cu")).read()
+    m = re.search(r"kWorkspaceBytes\s*=\s*(\d+)LL\s*<<\s*(\d+)", src)
+    assert m, "workspace size not found"
+    ws = int(m.group(1)) << int(m.group(2))
+    rng = np.random.default_rng(5)
+    for log2n in range(17, 29):
+        half = 1 << (log2n - 1)
+        rsg = ((half + 2 + 31) // 32) * 32
+        per_t = 2 * 4 * rsg * 4
+        chunk = max(1, ws // per_t)
+        words = chunk * 4 * rsg
+        assert words < 1 << 32, log2n
+        probes = [0, words - 1] + [k * rsg + d for k in range(1, 4 * chunk, max(1, 4 * chunk // 64))
+                                   for d in (-1, 0, 1)]
+        probes += [int(x) for x in rng.integers(0, words, 200)]
+        for w in probes:
+            assert _div_model(w, rsg) == w // rsg, (log2n, w)
